@@ -1,0 +1,230 @@
+"""FP64 CPU oracle of the bank matched filter -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  The library under ``paper_1006_4644_gb300`` never
+imports, links or calls it, and the two share no code.
+
+The arithmetic lives in ``cui_oracle.c`` (plain C, FP64, compiled with gcc on
+first use into ``oracle/_build``); this module only marshals numpy arrays.
+Each function names the part of the paper it follows:
+
+* ``segment_spectrum``  -- X(f) of eq:matchedfilter, d~_k = dt sum_j d_j e^{-2 pi i jk/N}
+* ``spa_phase`` / ``spa_template`` -- the post-Newtonian template of Sec.
+  "template generation", in its stationary-phase (TaylorF2) form
+* ``sigma2``           -- the normalisation <theta, theta> of step 1 of the
+  per-chunk loop (Sec. "Matched filtering")
+* ``correlate``        -- eq:matchedfilter on the sampled one-sided band
+* ``correlate_polarisations`` -- steps 2-3 of the per-chunk loop (two real
+  correlators c_+, c_x)
+* ``peak_triggers``    -- step 4 of the per-chunk loop (maximum above a
+  threshold), with the window reading of "local maximum"
+* ``fft`` / ``dft``    -- textbook radix-2 FFT and naive DFT used above
+
+Parity unpinned: the absolute constant of Psi (-pi/4 and the constant part of
+the 2.5PN logarithm) is a convention; it moves every reported phase by the
+same constant and changes no rho.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cui_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+# A prebuilt oracle library to load instead (the mutation tests point this at
+# deliberately broken copies of cui_oracle.c).
+_OVERRIDE = os.environ.get("CUI_ORACLE_LIB")
+_lock = threading.Lock()
+_lib = None
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_lp = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_L = C.c_long
+_D = C.c_double
+_PL = C.POINTER(C.c_long)
+_PD = C.POINTER(C.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, IEEE arithmetic) if stale."""
+    with _lock:
+        stale = force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC)
+        if stale:
+            os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+            tmp = _OUT + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+            os.replace(tmp, _OUT)
+    return _OUT
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = C.CDLL(_OVERRIDE or build())
+    lib.or_dft.argtypes = [_L, C.c_int, _dp, _dp, _dp, _dp]
+    lib.or_dft.restype = None
+    lib.or_fft.argtypes = [_L, C.c_int, _dp, _dp]
+    lib.or_fft.restype = C.c_int
+    lib.or_segment_spectrum.argtypes = [_L, _D, _dp, _dp, _dp]
+    lib.or_segment_spectrum.restype = C.c_int
+    lib.or_spa_phase.argtypes = [_D, _D, C.c_int, _L, _dp, _dp]
+    lib.or_spa_phase.restype = None
+    lib.or_template_band.argtypes = [_D, _D, _D, _D, _L, _PL, _PL]
+    lib.or_template_band.restype = None
+    lib.or_spa_template.argtypes = [_D, _D, C.c_int, _D, _D, _L, _dp, _dp, _PL, _PL]
+    lib.or_spa_template.restype = C.c_int
+    lib.or_sigma2.argtypes = [_L, _D, _dp, _dp, _dp, _L, _L]
+    lib.or_sigma2.restype = _D
+    lib.or_correlate.argtypes = [_L, _D, _dp, _dp, _dp, _dp, _dp, _L, _L, _dp, _dp]
+    lib.or_correlate.restype = C.c_int
+    lib.or_correlate_polarisations.argtypes = [_L, _D, _dp, _dp, _dp, _dp, _dp, _L, _L, _dp, _dp]
+    lib.or_correlate_polarisations.restype = C.c_int
+    lib.or_peak_triggers.argtypes = [_L, _dp, _dp, _D, _L, _L, _L, _D, _PL, _PD, _PD, _lp, _dp, _dp, _L]
+    lib.or_peak_triggers.restype = _L
+    lib.or_filter_template.argtypes = [_L, _D, _dp, _dp, _dp, _D, _D, C.c_int, _D, _L, _L, _L, _D,
+                                       _PD, _PL, _PD, _PD, _lp, _dp, _dp, _L]
+    lib.or_filter_template.restype = _L
+    _lib = lib
+    return lib
+
+
+def _f64(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _split(z):
+    z = np.asarray(z, dtype=np.complex128)
+    return _f64(z.real), _f64(z.imag)
+
+
+def dft(x, sign: int):
+    """Naive O(n^2) DFT, y_k = sum_j x_j exp(sign 2 pi i jk/n)."""
+    xr, xi = _split(x)
+    n = len(xr)
+    yr, yi = np.empty(n), np.empty(n)
+    _load().or_dft(n, int(sign), xr, xi, yr, yi)
+    return yr + 1j * yi
+
+
+def fft(x, sign: int):
+    """Radix-2 FFT with the same convention as ``dft`` (n a power of two)."""
+    xr, xi = _split(x)
+    xr, xi = xr.copy(), xi.copy()
+    if _load().or_fft(len(xr), int(sign), xr, xi) != 0:
+        raise ValueError("n must be a power of two")
+    return xr + 1j * xi
+
+
+def segment_spectrum(d, fs: float):
+    """d~_k = dt sum_j d_j exp(-2 pi i jk/n) for k = 0..n/2."""
+    d = _f64(d)
+    n = len(d)
+    dr, di = np.empty(n // 2 + 1), np.empty(n // 2 + 1)
+    if _load().or_segment_spectrum(n, float(fs), d, dr, di) != 0:
+        raise ValueError("n must be a power of two")
+    return dr + 1j * di
+
+
+def spa_phase(m1: float, m2: float, pn_x2: int, f):
+    f = _f64(np.atleast_1d(f))
+    out = np.empty_like(f)
+    _load().or_spa_phase(float(m1), float(m2), int(pn_x2), len(f), f, out)
+    return out
+
+
+def template_band(m1: float, m2: float, f_low: float, fs: float, n: int):
+    lo, hi = C.c_long(), C.c_long()
+    _load().or_template_band(float(m1), float(m2), float(f_low), float(fs), int(n), C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
+
+
+def spa_template(m1: float, m2: float, pn_x2: int, f_low: float, fs: float, n: int):
+    """(h~_k for k = 0..n/2, k_lo, k_hi)."""
+    hr, hi = np.empty(n // 2 + 1), np.empty(n // 2 + 1)
+    lo, kh = C.c_long(), C.c_long()
+    if _load().or_spa_template(float(m1), float(m2), int(pn_x2), float(f_low), float(fs), int(n),
+                               hr, hi, C.byref(lo), C.byref(kh)) != 0:
+        raise MemoryError("oracle template")
+    return hr + 1j * hi, lo.value, kh.value
+
+
+def sigma2(h, psd, fs: float, n: int, k_lo: int, k_hi: int) -> float:
+    hr, hi = _split(h)
+    return float(_load().or_sigma2(int(n), float(fs), hr, hi, _f64(psd), int(k_lo), int(k_hi)))
+
+
+def correlate(dtilde, h, psd, fs: float, n: int, k_lo: int, k_hi: int):
+    """z_j, j = 0..n-1 (complex128)."""
+    dr, di = _split(dtilde)
+    hr, hi = _split(h)
+    zr, zi = np.empty(n), np.empty(n)
+    if _load().or_correlate(int(n), float(fs), dr, di, hr, hi, _f64(psd), int(k_lo), int(k_hi), zr, zi) != 0:
+        raise ValueError("n must be a power of two")
+    return zr + 1j * zi
+
+
+def correlate_polarisations(dtilde, h, psd, fs: float, n: int, k_lo: int, k_hi: int):
+    """(c_plus, c_cross), the paper's two real correlators."""
+    dr, di = _split(dtilde)
+    hr, hi = _split(h)
+    cp, cx = np.empty(n), np.empty(n)
+    if _load().or_correlate_polarisations(int(n), float(fs), dr, di, hr, hi, _f64(psd), int(k_lo),
+                                          int(k_hi), cp, cx) != 0:
+        raise ValueError("n must be a power of two")
+    return cp, cx
+
+
+def peak_triggers(z, sig2: float, lo: int, hi: int, window: int, thr: float, cap: int = 1 << 16):
+    zr, zi = _split(z)
+    pj, pr, pp = C.c_long(), C.c_double(), C.c_double()
+    tj, tr, tp = np.empty(cap, dtype=np.int64), np.empty(cap), np.empty(cap)
+    cnt = _load().or_peak_triggers(len(zr), zr, zi, float(sig2), int(lo), int(hi), int(window), float(thr),
+                                   C.byref(pj), C.byref(pr), C.byref(pp), tj, tr, tp, int(cap))
+    m = min(cnt, cap)
+    return dict(peak_j=pj.value, peak_rho=pr.value, peak_phase=pp.value, n_trig=int(cnt),
+                trig_j=tj[:m].copy(), trig_rho=tr[:m].copy(), trig_phase=tp[:m].copy())
+
+
+def filter_template(dtilde, psd, m1: float, m2: float, pn_x2: int, f_low: float, fs: float, n: int,
+                    lo: int = 0, hi: int | None = None, window: int | None = None, thr: float = 6.0,
+                    cap: int = 1 << 16):
+    """One template through the per-chunk loop; returns a dict with sigma2,
+    the peak (j, rho, phase) and the triggers."""
+    hi = n if hi is None else hi
+    window = int(fs) if window is None else window
+    dr, di = _split(dtilde)
+    psd = _f64(psd)
+    s2, pj, pr, pp = C.c_double(), C.c_long(), C.c_double(), C.c_double()
+    tj, tr, tp = np.empty(cap, dtype=np.int64), np.empty(cap), np.empty(cap)
+    cnt = _load().or_filter_template(int(n), float(fs), dr, di, psd, float(m1), float(m2), int(pn_x2),
+                                     float(f_low), int(lo), int(hi), int(window), float(thr),
+                                     C.byref(s2), C.byref(pj), C.byref(pr), C.byref(pp), tj, tr, tp, int(cap))
+    if cnt < 0:
+        raise MemoryError("oracle filter")
+    m = min(cnt, cap)
+    return dict(sigma2=s2.value, peak_j=pj.value, peak_rho=pr.value, peak_phase=pp.value, n_trig=int(cnt),
+                trig_j=tj[:m].copy(), trig_rho=tr[:m].copy(), trig_phase=tp[:m].copy())
+
+
+def filter_bank(dtilde, psd, m1s, m2s, pn_x2: int, f_low: float, fs: float, n: int, lo: int = 0,
+                hi: int | None = None, window: int | None = None, thr: float = 6.0, threads: int | None = None):
+    """``filter_template`` over a bank, one template per worker thread (the C
+    call releases the GIL).  Returns a list of per-template dicts."""
+    threads = threads or len(os.sched_getaffinity(0))
+    dtilde = np.asarray(dtilde, dtype=np.complex128)
+    psd = _f64(psd)
+    _load()
+
+    def one(i):
+        return filter_template(dtilde, psd, m1s[i], m2s[i], pn_x2, f_low, fs, n, lo, hi, window, thr)
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(one, range(len(m1s))))
