@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Bank matched-filter benchmark: templates/s on one 2^20-sample segment.
+
+One step = one pass of the whole hot path over one segment: upload and
+transform the segment (FP64 FFT, noise weighting, every template's sigma),
+then filter the whole bank (fused generate x correlate -> two-pass FFT ->
+|z|^2 peak / threshold reduction) with peaks and triggers left on the device.
+Workload (default): N = 2^20 at 4096 Hz (256 s), 1024 3.5PN templates with
+m1, m2 uniform in [1, 10] Msun, f_low = 30 Hz, 5 injections at SNR 8-15,
+synthetic coloured Gaussian noise.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "templates/s on 2^20-sample segments, mixed vs plain, at SNR rel err <=1e-3"
+UNIT = "templates/s"
+DEFAULT_WORKLOAD = "seg256s_bank1024_pn35"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_digest() -> str:
+    """Digest of the fused kernels' source, to tell whether a stored ncu
+    capture still describes them."""
+    h = hashlib.sha256()
+    for f in ("fused.cu", "common.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1006_4644_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel: str, workload: str):
+    """DRAM bytes per template of `kernel` from a committed ncu summary, or None
+    when absent or taken on other source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"dram_bytes_per_template:\s*([0-9.eE+]+)", text)
+    d = re.search(r"source_digest:\s*([0-9a-f]+)", text)
+    if not m or not d or d.group(1) != source_digest():
+        return None
+    return float(m.group(1))
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.file:
+            return None
+        self.file.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_segment(w, bank, psd):
+    """Noise plus the workload's injections.  The injected waveforms are the
+    library's own templates (cui_bank_template) scaled by its sigma."""
+    import numpy as np
+    import torch
+
+    import synth
+
+    d = w.noise()
+    strain0 = synth.strain_from_spectrum(d, w.n, w.fs)
+    bank.upload(strain0, psd)
+    sig = bank.sigma()
+    out = torch.zeros(w.n // 2 + 1, dtype=torch.complex64, device="cuda")
+    for t, j0, snr in zip(*w.injection_plan()):
+        bank.template(int(t), out)
+        h = out.cpu().numpy().astype(np.complex128)
+        synth.add_signal(d, h, float(snr) / sig[t], int(j0), w.n)
+    return synth.strain_from_spectrum(d, w.n, w.fs)
+
+
+def cpu_baseline(w, budget_s: float = 15.0, per_step: int | None = None):
+    """The FP64 oracle as it stands, on this host's cores, on a bounded sample
+    of the same workload (noise plus oracle-built injections)."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    psd = w.psd()
+    d = w.noise()
+    m1, m2 = w.masses()
+    for t, j0, snr in zip(*w.injection_plan()):
+        h, lo, hi = oracle.spa_template(m1[t], m2[t], w.pn_x2, w.f_low, w.fs, w.n)
+        synth.add_signal(d, h, float(snr) / math.sqrt(oracle.sigma2(h, psd, w.fs, w.n, lo, hi)), int(j0), w.n)
+    strain = synth.strain_from_spectrum(d, w.n, w.fs)
+    dt = oracle.segment_spectrum(strain, w.fs)
+    t0 = time.perf_counter()
+    oracle.filter_template(dt, psd, m1[0], m2[0], w.pn_x2, w.f_low, w.fs, w.n)
+    one = time.perf_counter() - t0
+    if per_step is None:
+        per_step = int(max(cores, min(w.n_templates, budget_s * cores / max(one, 1e-3))))
+    sel = np.arange(per_step) % w.n_templates
+    t0 = time.perf_counter()
+    oracle.filter_bank(dt, psd, m1[sel], m2[sel], w.pn_x2, w.f_low, w.fs, w.n, threads=cores)
+    el = time.perf_counter() - t0
+    return {"value": per_step / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{per_step} templates of {w.name} (segment FFT excluded, one template per thread)",
+            "seconds": el}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores = len(os.sched_getaffinity(0))
+    # size each step to ~5 s of oracle work so the whole run stays short
+    probe = cpu_baseline(w, per_step=cores)
+    per_step = int(max(cores, probe["value"] * 5.0))
+    for _ in range(args.warmup):
+        cpu_baseline(w, per_step=cores)
+    tot, n = 0.0, 0
+    for _ in range(args.steps):
+        r = cpu_baseline(w, per_step=per_step)
+        tot += r["seconds"]
+        n += per_step
+    value = n / tot
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "templates": w.n_templates, "sample_per_step": per_step},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} templates per step of {w.name}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--flags", type=int, default=0, help="extra CUI_* flags for the fused path")
+    ap.add_argument("--plain-templates", type=int, default=64)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    import synth
+
+    w = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1006_4644_gb300 import CUI_PLAIN, Bank
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    # weak scaling: every rank filters its own bank of the workload's size
+    m1, m2 = synth.sample_masses(w.seed, 1 + 7919 * rank, w.n_templates, w.mass_lo, w.mass_hi, w.mass_log)
+    psd = w.psd()
+    stream = torch.cuda.current_stream()
+    bank = Bank(m1, m2, n=w.n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, flags=args.flags, stream=stream.cuda_stream)
+    strain = build_segment(w, bank, psd)
+    strain_d = torch.from_numpy(strain).cuda()
+    psd_fin = psd.copy()
+    psd_fin[0] = 1.0  # bin 0 is never read
+    psd_d = torch.from_numpy(psd_fin).cuda()
+    peaks_d = torch.empty(w.n_templates * 16, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+
+    def step():
+        bank.upload(strain_d, psd_d)
+        bank.filter(peaks_dev=peaks_d)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    bank.trace_read()
+    bank.trace(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for a, b in ev:
+            flush.zero_()  # L2 flushed between steps, outside the timed interval
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    bank.trace(False)
+    trace = bank.trace_read()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = w.n_templates * args.steps * world / (t_ms / 1e3)
+
+    # roofline of the dominant kernel: algorithmic bytes = one write (pass 1)
+    # or one read (pass 2) of the N-point complex64 spectrum per template
+    per_tmpl = w.n * (4 if args.flags & 2 else 8)
+    launches = sum(v[0] for v in trace.values())
+    p1 = trace.get("pass1", (0, 0, 0.0))
+    p2 = trace.get("pass2", (0, 0, 0.0))
+    dom, dv = ("pass2", p2) if p2[2] >= p1[2] else ("pass1", p1)
+    n_units = w.n_templates * args.steps
+    peak, peak_src = measured_hbm()
+    achieved = n_units * per_tmpl / (dv[2] / 1e3) / 1e9
+    traffic = stored_traffic(dom, w.name)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic * n_units / max(1, dv[1]) if traffic is not None else None,
+            "kernel": dom, "peak_source": peak_src,
+            "avg_launch_ms": dv[2] / max(1, dv[1]), "templates_per_launch": n_units / max(1, dv[1]),
+            "both_passes": {"achieved": n_units * 2 * per_tmpl / ((p1[2] + p2[2]) / 1e3) / 1e9,
+                            "frac": n_units * 2 * per_tmpl / ((p1[2] + p2[2]) / 1e3) / 1e9 / peak},
+            "kernel_ms": {k: v[2] for k, v in trace.items()}}
+
+    # end to end through the public API with pinned host buffers
+    strain_h = torch.from_numpy(strain).pin_memory()
+    psd_h = torch.from_numpy(psd_fin).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+    bank2 = Bank(m1, m2, n=w.n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, flags=args.flags, stream=stream.cuda_stream)
+    n_trig = 0
+
+    def e2e_step():
+        nonlocal n_trig
+        bank2.upload(strain_h.numpy(), psd_h.numpy())
+        bank2.filter()
+        bank2.peaks()
+        tr, n_trig = bank2.triggers()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": w.n_templates * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": w.n * 8 + (w.n // 2 + 1) * 8,
+           "d2h_bytes_per_step": w.n_templates * 16 + n_trig * 24 + 8}
+    bank2.close()
+
+    # the plain per-template FP32 path on a subset of the bank, same segment
+    plain = None
+    if args.plain_templates > 0:
+        npl = min(args.plain_templates, w.n_templates)
+        pb = Bank(m1, m2, n=w.n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, flags=CUI_PLAIN, stream=stream.cuda_stream)
+        pb.upload(strain_d, psd_d)
+        order = np.arange(npl)
+        pb.filter(order)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        reps = 3
+        for _ in range(reps):
+            pb.upload(strain_d, psd_d)
+            pb.filter(order)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pv = npl * reps / (a.elapsed_time(b) / 1e3)
+        plain = {"value": pv, "unit": UNIT, "templates": npl, "mixed_over_plain": value / pv}
+        pb.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w)
+        cpu.pop("seconds", None)
+
+    bank.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "n": w.n, "fs": w.fs, "templates_per_gpu": w.n_templates,
+                           "pn_order": w.pn_x2 / 2, "f_low": w.f_low, "mass_range": [w.mass_lo, w.mass_hi],
+                           "injections": w.n_inj, "l2": "flushed between steps (256 MiB write)",
+                           "phase": "fp32 pair anchors" if args.flags & 1 else "fp64 anchors + fp32 cubic",
+                           "storage": "bf16x2" if args.flags & 2 else "complex64",
+                           "parallelism": f"bank replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "plain": plain, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

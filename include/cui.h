@@ -1,0 +1,186 @@
+/*
+ * cui.h -- C ABI of the GB300 bank matched filter.
+ *
+ * The library matched-filters one detector segment against a bank of
+ * stationary-phase post-Newtonian inspiral templates and reduces the
+ * normalised correlator |z|^2 / sigma^2 to a peak and threshold triggers per
+ * template.  It follows the paper's problem statement (Bosi,
+ * arXiv:1006.4644, Sec. "Matched filtering"): a bank of (m1, m2) points, a
+ * data chunk with its noise power spectrum, the correlator of
+ * eq:matchedfilter for each template, normalised so that <theta, theta> = 1,
+ * its maximum above a threshold, and a reduction of those maxima.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a cui_status; nothing throws across the ABI.  A
+ *    failing call leaves a message for cui_last_error() (thread-local).
+ *  - Work is enqueued asynchronously on desc.stream (a cudaStream_t; NULL is
+ *    the legacy default stream).  cui_triggers, cui_peaks and cui_bank_sigma
+ *    synchronise that stream before they return.
+ *  - Input pointers are not retained: the library copies what it needs into
+ *    memory it owns.  Pointers documented as "device" must be device (or
+ *    managed) memory of the current device; all others are host memory.
+ *  - A handle is used by one host thread at a time; calls on one handle are
+ *    not re-entrant.  Distinct handles are independent.
+ *  - Units: masses in solar masses, frequencies in Hz, the PSD in 1/Hz
+ *    (one-sided), the strain dimensionless, samples at desc.sample_rate.
+ *
+ * Definitions (k = one-sided frequency bin, f_k = k fs / N, df = fs / N):
+ *   d~_k   = (1/fs) sum_j d_j exp(-2 pi i j k / N)
+ *   h~_k   = f_k^(-7/6) exp(-i Psi(f_k)) for k_lo <= k < k_hi, else 0, where
+ *            Psi is the TaylorF2 phase (t_c = 0, phi_c = 0) truncated at
+ *            twice-PN-order pn_order_x2, k_lo = ceil(f_low / df) and
+ *            k_hi = min(ceil(f_ISCO / df), N/2), f_ISCO = 1 / (6^1.5 pi M)
+ *   sigma^2 = 4 df sum_k |h~_k|^2 / S_k
+ *   z_j    = 4 df sum_k d~_k conj(h~_k) / S_k exp(+2 pi i j k / N), j in [0, N)
+ *   rho_j  = |z_j| / sigma,  phase_j = arg z_j
+ *   peak   = argmax of rho over [valid_lo, valid_hi), lowest sample on ties
+ *   triggers: one per window [valid_lo + m W, valid_lo + (m+1) W) (clipped to
+ *            valid_hi) whose maximum rho exceeds snr_threshold (strictly).
+ */
+#ifndef CUI_H
+#define CUI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CUI_OK = 0,
+    CUI_ERR_ARG = 1,      /* invalid argument (message says which)             */
+    CUI_ERR_CUDA = 2,     /* a CUDA runtime call failed                         */
+    CUI_ERR_OOM = 3,      /* device memory allocation failed                    */
+    CUI_ERR_STATE = 4,    /* call out of order (e.g. filter before upload)      */
+    CUI_ERR_OVERFLOW = 5, /* more triggers than the buffer holds; n_total exact */
+    CUI_ERR_TIMEOUT = 6   /* a bounded device wait gave up; handle stays usable */
+} cui_status;
+
+/* desc.flags */
+#define CUI_PSI_DF      0x1u /* fused path: anchor phases in double-float (FP32 pairs) instead of FP64 */
+#define CUI_STORE_BF16  0x2u /* fused path: store the spectrum between FFT passes as bf16 pairs */
+#define CUI_PLAIN       0x4u /* per-template unfused path: generate, multiply, multi-pass FFT, detect */
+#define CUI_PLAIN_FP64  0x8u /* with CUI_PLAIN: template, product and FFT in FP64 (else FP32) */
+
+typedef struct cui_bank_s *cui_bank; /* opaque; owns every device buffer it allocates */
+
+typedef struct {
+    int32_t pn_order_x2;      /* twice the PN order of the phase, 0..7 (4 = 2.0PN, 7 = 3.5PN) */
+    int32_t reserved0;        /* must be 0 */
+    double f_low;             /* lower cut-off (Hz), > 0 */
+    double sample_rate;       /* fs (Hz), > 0 */
+    int64_t n;                /* segment length N: a power of two, 2^6 .. 2^22 */
+    uint32_t flags;           /* CUI_* flags above */
+    uint32_t reserved1;       /* must be 0 */
+    double snr_threshold;     /* trigger threshold on rho (default reading: 6) */
+    int64_t window;           /* trigger window W in samples, >= 1 */
+    int64_t valid_lo;         /* samples considered: [valid_lo, valid_hi), 0 <= lo <= hi <= N */
+    int64_t valid_hi;
+    int64_t trigger_capacity; /* device trigger records; 0 selects 1 << 20 */
+    void *stream;             /* cudaStream_t for all work of this handle */
+} cui_bank_desc;
+
+typedef struct {
+    int64_t sample; /* argmax j of rho over the valid range */
+    float snr;      /* rho at that sample */
+    float phase;    /* arg z at that sample (radians) */
+} cui_peak;
+
+typedef struct {
+    int32_t tmpl;   /* template index in the bank */
+    int32_t pad;
+    int64_t sample; /* sample of the window maximum */
+    float snr;      /* rho there, > snr_threshold */
+    float phase;    /* arg z there */
+} cui_trigger;
+
+/* Build a bank of n_templates templates (m1[i], m2[i]), host arrays that are
+ * copied.  Allocates the handle's device memory and per-template constants on
+ * the current device; enqueues set-up work on desc->stream.
+ * Errors: CUI_ERR_ARG (bad desc field, n_templates < 1, masses <= 0 or not
+ * finite), CUI_ERR_OOM, CUI_ERR_CUDA.  *out is NULL on failure.
+ * Paper: the bank of (m1, m2) points (Sec. "Matched filtering") and
+ * host_template_init / device_template_init (Sec. "Pipeline main details"). */
+cui_status cui_bank_create(const cui_bank_desc *desc, const double *m1, const double *m2,
+                           int64_t n_templates, cui_bank *out);
+
+/* Upload one segment: strain d_j (n = desc.n FP64 samples) and its one-sided
+ * PSD S_k (n_psd = N/2 + 1 FP64 values, 1/Hz; only bins in [k_lo, N/2) are
+ * read and must be finite and > 0).  on_device = 1 means both pointers are
+ * device memory, 0 host memory (pinned host memory makes the copies
+ * asynchronous).  Computes d~ in FP64, the noise-weighted data and every
+ * template's sigma^2 on the device.
+ * Errors: CUI_ERR_ARG (n != desc.n, n_psd != N/2 + 1, NULL pointers),
+ * CUI_ERR_CUDA.  Paper: the data chunk X(f) and S_n(f) of eq:matchedfilter. */
+cui_status cui_segment_upload(cui_bank bank, const double *strain, int64_t n, const double *psd,
+                              int64_t n_psd, int on_device);
+
+/* Filter `count` templates of the bank against the uploaded segment.  order:
+ * host array of distinct template indices in [0, n_templates), or NULL for all
+ * templates in bank order (count must then equal n_templates).  peaks_dev:
+ * device array of n_templates records (caller-owned) receiving the peak of
+ * every filtered template at its template index, or NULL to keep peaks in the
+ * handle (read them with cui_peaks).  Triggers of this call replace those of
+ * the previous call.  Asynchronous.
+ * Errors: CUI_ERR_STATE (no segment uploaded), CUI_ERR_ARG, CUI_ERR_CUDA.
+ * Paper: the per-chunk loop of Sec. "Matched filtering", steps 1-4. */
+cui_status cui_filter_bank(cui_bank bank, const int32_t *order, int64_t count, cui_peak *peaks_dev);
+
+/* Copy the peaks of the last filter call that kept them in the handle to
+ * host_out[0 .. count), indexed by template (count <= n_templates).
+ * Synchronises.  Errors: CUI_ERR_ARG, CUI_ERR_STATE, CUI_ERR_CUDA,
+ * CUI_ERR_TIMEOUT. */
+cui_status cui_peaks(cui_bank bank, cui_peak *host_out, int64_t count);
+
+/* Copy the triggers of the last filter call to host_out and their exact total
+ * number to *n_total.  min(*n_total, capacity, desc.trigger_capacity) records
+ * are written, sorted by (tmpl, sample).  When the device buffer
+ * (desc.trigger_capacity) overflowed, the records kept are an arbitrary
+ * subset; peaks are unaffected.  Synchronises.  Returns CUI_ERR_OVERFLOW when
+ * *n_total exceeds `capacity` or the device buffer, CUI_ERR_TIMEOUT if a
+ * bounded device wait gave up during the call.
+ * Paper: the candidate set {t_0^i} of step 4 and its reduction. */
+cui_status cui_triggers(cui_bank bank, cui_trigger *host_out, int64_t capacity, int64_t *n_total);
+
+/* sigma_t = sqrt(4 df sum_k |h~_k|^2 / S_k) of every template for the
+ * uploaded PSD, to host_sigma[0 .. n_templates).  Synchronises.
+ * Errors: CUI_ERR_STATE (no segment), CUI_ERR_CUDA.
+ * Paper: the template normalisation of step 1 ("normalization", Sec.
+ * "template generation and normalization"). */
+cui_status cui_bank_sigma(cui_bank bank, double *host_sigma);
+
+/* Write template t as the fused path generates it: h~_k for k = 0 .. N/2 as
+ * N/2 + 1 interleaved FP32 (re, im) pairs to device memory out_dev, zero
+ * outside [k_lo, k_hi).  Asynchronous.  Errors: CUI_ERR_ARG, CUI_ERR_CUDA.
+ * Paper: device_template_proc (Sec. "Pipeline main details"). */
+cui_status cui_bank_template(cui_bank bank, int64_t t, float *out_dev);
+
+/* Tracing.  With tracing on, every call records CUDA events on desc.stream
+ * around each group of kernels it launches ("segment", "pass1", "pass2",
+ * "finalize", "plain"); cui_trace_read synchronises, writes up to `capacity`
+ * per-group totals (launches of this library's kernels, summed event time)
+ * to host_out, the number of groups to *n, and clears the record.
+ * Errors: CUI_ERR_ARG, CUI_ERR_CUDA.  Paper: the per-step timing information
+ * of Sec. "GPU based detection pipeline performances and profiling". */
+typedef struct {
+    char name[24];
+    int64_t launches; /* kernel launches in this group */
+    int64_t calls;    /* timed intervals */
+    double ms;        /* total event time */
+} cui_trace_stat;
+
+cui_status cui_trace_enable(cui_bank bank, int on);
+cui_status cui_trace_read(cui_bank bank, cui_trace_stat *host_out, int64_t capacity, int64_t *n);
+
+/* Release every resource of the handle (synchronises its stream first).
+ * NULL is allowed. */
+void cui_bank_destroy(cui_bank bank);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *cui_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUI_H */

@@ -1,0 +1,86 @@
+"""ctypes binding of ``libcui.so`` (include/cui.h).  Argument marshalling only:
+every step of the filter runs in the CUDA library.  Loading fails loudly when
+the library has not been built; there is no fallback."""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libcui.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "cui.h")
+
+CUI_OK, CUI_ERR_ARG, CUI_ERR_CUDA, CUI_ERR_OOM, CUI_ERR_STATE, CUI_ERR_OVERFLOW, CUI_ERR_TIMEOUT = range(7)
+STATUS_NAMES = {0: "CUI_OK", 1: "CUI_ERR_ARG", 2: "CUI_ERR_CUDA", 3: "CUI_ERR_OOM", 4: "CUI_ERR_STATE",
+                5: "CUI_ERR_OVERFLOW", 6: "CUI_ERR_TIMEOUT"}
+CUI_PSI_DF, CUI_STORE_BF16, CUI_PLAIN, CUI_PLAIN_FP64 = 0x1, 0x2, 0x4, 0x8
+
+
+class cui_bank_desc(C.Structure):
+    _fields_ = [("pn_order_x2", C.c_int32), ("reserved0", C.c_int32), ("f_low", C.c_double),
+                ("sample_rate", C.c_double), ("n", C.c_int64), ("flags", C.c_uint32), ("reserved1", C.c_uint32),
+                ("snr_threshold", C.c_double), ("window", C.c_int64), ("valid_lo", C.c_int64),
+                ("valid_hi", C.c_int64), ("trigger_capacity", C.c_int64), ("stream", C.c_void_p)]
+
+
+class cui_trace_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("calls", C.c_int64), ("ms", C.c_double)]
+
+
+PEAK_DTYPE = np.dtype([("sample", "<i8"), ("snr", "<f4"), ("phase", "<f4")])
+TRIGGER_DTYPE = np.dtype([("tmpl", "<i4"), ("pad", "<i4"), ("sample", "<i8"), ("snr", "<f4"), ("phase", "<f4")])
+
+
+class CuiError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libcui.so (built by ``paper_1006_4644_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    lib.cui_bank_create.argtypes = [C.POINTER(cui_bank_desc), vp, vp, C.c_int64, C.POINTER(vp)]
+    lib.cui_segment_upload.argtypes = [vp, vp, C.c_int64, vp, C.c_int64, C.c_int]
+    lib.cui_filter_bank.argtypes = [vp, vp, C.c_int64, vp]
+    lib.cui_peaks.argtypes = [vp, vp, C.c_int64]
+    lib.cui_triggers.argtypes = [vp, vp, C.c_int64, C.POINTER(C.c_int64)]
+    lib.cui_bank_sigma.argtypes = [vp, vp]
+    lib.cui_bank_template.argtypes = [vp, C.c_int64, vp]
+    lib.cui_trace_enable.argtypes = [vp, C.c_int]
+    lib.cui_trace_read.argtypes = [vp, C.POINTER(cui_trace_stat), C.c_int64, C.POINTER(C.c_int64)]
+    lib.cui_bank_destroy.argtypes = [vp]
+    lib.cui_bank_destroy.restype = None
+    lib.cui_last_error.restype = C.c_char_p
+    for name in ("cui_bank_create", "cui_segment_upload", "cui_filter_bank", "cui_peaks", "cui_triggers",
+                 "cui_bank_sigma", "cui_bank_template", "cui_trace_enable", "cui_trace_read"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/cui.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cui_[a-z_0-9]+)\s*\(", text)))
+
+
+def check(status: int, where: str):
+    if status != CUI_OK:
+        raise CuiError(status, where, load().cui_last_error().decode())
+    return status

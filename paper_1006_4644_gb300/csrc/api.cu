@@ -1,0 +1,713 @@
+// C ABI of the bank matched filter (include/cui.h): argument checking, the
+// per-template constants, device buffers and the order of kernel launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace cui;
+
+namespace {
+
+thread_local std::string g_err;
+
+cui_status fail(cui_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+cui_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(CUI_ERR_OOM, "%s: out of device memory", what);
+    }
+    return fail(CUI_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUI_TRY(call, what)                                                                                          \
+    do {                                                                                                             \
+        cudaError_t e_ = (call);                                                                                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);                                                           \
+    } while (0)
+
+constexpr double kMsunS = 4.925490947e-6; // G M_sun / c^3 (s)
+constexpr double kEuler = 0.57721566490153286061;
+
+bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+int ilog2(int64_t n)
+{
+    int l = 0;
+    while ((int64_t(1) << l) < n) ++l;
+    return l;
+}
+
+// binom(p, n) for real p
+double binom(double p, int n)
+{
+    double r = 1.0;
+    for (int m = 0; m < n; ++m) r *= (p - m) / (m + 1);
+    return r;
+}
+
+DerivConsts make_deriv_consts()
+{
+    const double pw[kNB] = {-5.0 / 3, -1.0, -2.0 / 3, -1.0 / 3, 0.0, 0.0, 1.0 / 3, 0.0, 2.0 / 3};
+    DerivConsts dc;
+    std::memset(&dc, 0, sizeof dc);
+    for (int n = 1; n < 4; ++n) {
+        for (int i = 0; i < kNB; ++i) {
+            if (i == 4 || i == 5) dc.B[n][i] = 0.f; // constant; ln k handled by lam
+            else if (i == 7) dc.B[n][i] = (float)binom(1.0 / 3, n);
+            else dc.B[n][i] = (float)binom(pw[i], n);
+        }
+        dc.lam[n] = (float)((n % 2 ? 1.0 : -1.0) / n);
+        double g = 0.0;
+        for (int m = 0; m < n; ++m) g += binom(1.0 / 3, m) * (((n - m) % 2 ? 1.0 : -1.0) / (n - m));
+        dc.gam[n] = (float)g;
+    }
+    return dc;
+}
+
+// Phase of template (m1, m2) as Phi(k) = sum_i c_i g_i(k) in cycles, with
+// g = {k^-5/3, k^-1, k^-2/3, k^-1/3, 1, ln k, k^1/3, k^1/3 ln k, k^2/3}: the
+// TaylorF2 phase Psi(f) = -pi/4 + 3/(128 eta v^5) sum_i alpha_i v^i at
+// f = k df, v = u k^(1/3), u = (pi M df)^(1/3), with ln v expanded.
+void phase_coefficients(double m1, double m2, int pn, double df, double *c)
+{
+    const double pi = kPi;
+    const double M = (m1 + m2) * kMsunS;
+    const double eta = m1 * m2 / ((m1 + m2) * (m1 + m2));
+    const double P = 3.0 / (128.0 * eta);
+    const double u = std::cbrt(pi * M * df);
+    const double a2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
+    const double a3 = -16.0 * pi;
+    const double a4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta * eta;
+    const double A5 = pi * (38645.0 / 756.0 - 65.0 / 9.0 * eta);
+    const double A6 = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi * pi - 6848.0 / 21.0 * kEuler +
+                      eta * (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi * pi) + 76055.0 / 1728.0 * eta * eta -
+                      127825.0 / 1296.0 * eta * eta * eta;
+    const double a7 = pi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
+    double r[kNB] = {0};
+    r[0] = P * std::pow(u, -5.0);
+    if (pn >= 2) r[1] = P * a2 * std::pow(u, -3.0);
+    if (pn >= 3) r[2] = P * a3 * std::pow(u, -2.0);
+    if (pn >= 4) r[3] = P * a4 / u;
+    r[4] = -pi / 4.0;
+    if (pn >= 5) {
+        r[4] += P * A5 * (1.0 + 3.0 * std::log(u * std::sqrt(6.0)));
+        r[5] = P * A5;
+    }
+    if (pn >= 6) {
+        r[6] = P * u * (A6 - 6848.0 / 21.0 * std::log(4.0 * u));
+        r[7] = -P * u * 6848.0 / 63.0;
+    }
+    if (pn >= 7) r[8] = P * a7 * u * u;
+    for (int i = 0; i < kNB; ++i) c[i] = r[i] / (2.0 * pi);
+}
+
+// First bin from which the per-row cubic of the fused path is accurate: its
+// remainder is dominated by the leading k^(-5/3) term,
+// |binom(-5/3, 4)| |c_0| k^(-5/3) (C/2 / k)^4, kept below kExactTol cycles
+// with a safety factor of 4.  Bins below it get the exact per-bin phase.
+constexpr double kExactTol = 1e-6;
+constexpr int kExactMax = 1 << 16;
+int exact_bound(double c0, int ccols, int64_t nh)
+{
+    const double h = ccols / 2.0;
+    const double k = std::pow(4.0 * 3.1701 * std::fabs(c0) * h * h * h * h / kExactTol, 3.0 / 17.0);
+    return (int)std::min<double>(std::ceil(k), (double)std::min<int64_t>(nh, kExactMax));
+}
+
+template <typename T> cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+} // namespace
+
+struct cui_bank_s {
+    cui_bank_desc desc;
+    cudaStream_t stream = nullptr;
+    int log2n = 0;
+    int64_t n = 0, nh = 0, nt = 0;
+    int k_low = 0;
+    double df = 0;
+    bool fused = false, plain_fp64 = false;
+    int nwin = 0;
+    // per template
+    std::vector<int32_t> h_khi;
+    double *d_coef = nullptr;
+    float2 *d_coef_df = nullptr;
+    double *d_mass = nullptr;
+    int32_t *d_khi = nullptr;
+    double *d_sigma2 = nullptr;
+    float *d_invnorm = nullptr;
+    Slot *d_peak = nullptr;
+    cui_peak *d_peaks = nullptr;
+    int32_t *d_iota = nullptr;
+    // segment
+    double *d_strain = nullptr, *d_psd = nullptr, *d_amp = nullptr, *d_prefix = nullptr, *d_scan = nullptr;
+    double2 *d_fa = nullptr, *d_fb = nullptr;
+    float2 *d_wbar = nullptr;
+    void *d_dS = nullptr;
+    SegScales *d_scales = nullptr;
+    // fused
+    int n1 = 0, n2 = 0, ccols = 0, rpc = 0, batch = 0;
+    double *d_basis = nullptr;
+    float2 *d_basis_df = nullptr;
+    int32_t *d_kex = nullptr;
+    float2 *d_gexact = nullptr;
+    std::vector<int32_t> h_kex;
+    int kx = 0;
+    void *d_y = nullptr;
+    Slot *d_win = nullptr;
+    // plain
+    void *d_h = nullptr, *d_qa = nullptr, *d_qb = nullptr;
+    double *d_acc = nullptr;
+    Slot *d_pwin = nullptr;
+    // outputs
+    cui_trigger *d_trig = nullptr;
+    int64_t trig_cap = 0;
+    unsigned long long *d_trig_count = nullptr;
+    int *d_err = nullptr;
+    int32_t *d_order = nullptr;
+    int64_t order_cap = 0;
+    bool have_segment = false, have_peaks = false;
+    // tracing: (group, start, stop, launches) per recorded interval
+    bool trace = false;
+    struct Mark {
+        int group;
+        cudaEvent_t a, b;
+        long long launches;
+    };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> pool;
+};
+
+namespace cui {
+std::atomic<long long> g_launches{0};
+}
+
+namespace {
+const char *const kGroups[] = {"segment", "pass1", "pass2", "finalize", "plain"};
+constexpr int kNGroups = 5;
+
+cudaEvent_t take_event(cui_bank b)
+{
+    if (!b->pool.empty()) {
+        cudaEvent_t e = b->pool.back();
+        b->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Opens a traced interval of `group` on the bank's stream; close() ends it.
+struct Span {
+    cui_bank b;
+    int group;
+    cudaEvent_t a = nullptr;
+    long long l0 = 0;
+    Span(cui_bank b_, int g) : b(b_), group(g)
+    {
+        if (!b->trace) return;
+        a = take_event(b);
+        l0 = g_launches.load();
+        cudaEventRecord(a, b->stream);
+    }
+    void close()
+    {
+        if (!b->trace || !a) return;
+        cudaEvent_t e = take_event(b);
+        cudaEventRecord(e, b->stream);
+        b->marks.push_back({group, a, e, g_launches.load() - l0});
+        a = nullptr;
+    }
+    ~Span() { close(); }
+};
+} // namespace
+
+static void release(cui_bank b)
+{
+    void *ptrs[] = {b->d_coef, b->d_coef_df, b->d_mass, b->d_khi, b->d_sigma2, b->d_invnorm, b->d_peak, b->d_peaks,
+                    b->d_iota, b->d_strain, b->d_psd, b->d_amp, b->d_prefix, b->d_scan, b->d_fa, b->d_fb,
+                    b->d_wbar, b->d_dS, b->d_scales, b->d_basis, b->d_basis_df, b->d_kex, b->d_gexact, b->d_y,
+                    b->d_win, b->d_h, b->d_qa, b->d_qb, b->d_acc, b->d_pwin, b->d_trig, b->d_trig_count, b->d_err,
+                    b->d_order};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (auto &m : b->marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (cudaEvent_t e : b->pool) cudaEventDestroy(e);
+}
+
+extern "C" const char *cui_last_error(void) { return g_err.c_str(); }
+
+extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m1, const double *m2,
+                                      int64_t n_templates, cui_bank *out)
+{
+    if (!out) return fail(CUI_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!desc || !m1 || !m2) return fail(CUI_ERR_ARG, "desc, m1 and m2 must be non-NULL");
+    const cui_bank_desc &d = *desc;
+    if (!is_pow2(d.n) || d.n < 64 || d.n > (int64_t(1) << 22))
+        return fail(CUI_ERR_ARG, "n = %lld must be a power of two in [2^6, 2^22]", (long long)d.n);
+    if (d.pn_order_x2 < 0 || d.pn_order_x2 > 7) return fail(CUI_ERR_ARG, "pn_order_x2 must be in 0..7");
+    if (d.reserved0 != 0 || d.reserved1 != 0) return fail(CUI_ERR_ARG, "reserved fields must be 0");
+    if (!(d.sample_rate > 0) || !std::isfinite(d.sample_rate)) return fail(CUI_ERR_ARG, "sample_rate must be > 0");
+    if (!(d.f_low > 0) || !std::isfinite(d.f_low)) return fail(CUI_ERR_ARG, "f_low must be > 0");
+    if (d.window < 1) return fail(CUI_ERR_ARG, "window must be >= 1");
+    if (d.valid_lo < 0 || d.valid_hi < d.valid_lo || d.valid_hi > d.n)
+        return fail(CUI_ERR_ARG, "need 0 <= valid_lo <= valid_hi <= n");
+    if (!std::isfinite(d.snr_threshold) || d.snr_threshold < 0) return fail(CUI_ERR_ARG, "snr_threshold must be >= 0");
+    if (d.trigger_capacity < 0) return fail(CUI_ERR_ARG, "trigger_capacity must be >= 0");
+    if (d.flags & ~(CUI_PSI_DF | CUI_STORE_BF16 | CUI_PLAIN | CUI_PLAIN_FP64)) return fail(CUI_ERR_ARG, "unknown flags");
+    if (n_templates < 1 || n_templates > (int64_t(1) << 31) - 1) return fail(CUI_ERR_ARG, "n_templates out of range");
+    for (int64_t i = 0; i < n_templates; ++i)
+        if (!(m1[i] > 0) || !(m2[i] > 0) || !std::isfinite(m1[i]) || !std::isfinite(m2[i]))
+            return fail(CUI_ERR_ARG, "template %lld: masses must be finite and > 0", (long long)i);
+
+    cui_bank b = new cui_bank_s();
+    b->desc = d;
+    b->stream = (cudaStream_t)d.stream;
+    b->n = d.n;
+    b->nh = d.n / 2;
+    b->log2n = ilog2(d.n);
+    b->nt = n_templates;
+    b->df = d.sample_rate / (double)d.n;
+    b->k_low = std::max<int>(1, (int)std::ceil(d.f_low / b->df));
+    b->fused = !(d.flags & CUI_PLAIN) && fused_supported(b->log2n);
+    b->plain_fp64 = (d.flags & CUI_PLAIN) && (d.flags & CUI_PLAIN_FP64);
+    b->nwin = (int)((d.valid_hi - d.valid_lo + d.window - 1) / d.window);
+    b->trig_cap = d.trigger_capacity ? d.trigger_capacity : (int64_t(1) << 20);
+    const int64_t nt = n_templates;
+    const int pn = d.pn_order_x2;
+
+    // per-template constants on the host
+    std::vector<double> coef(nt * kNB), mass(2 * nt);
+    std::vector<float2> coef_df(nt * kNB);
+    std::vector<int32_t> iota(nt);
+    b->h_khi.resize(nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        const double M = (m1[t] + m2[t]) * kMsunS;
+        const double f_isco = 1.0 / (std::pow(6.0, 1.5) * kPi * M);
+        const double kh = std::ceil(f_isco / b->df);
+        b->h_khi[t] = (int32_t)std::min<double>(kh, (double)b->nh);
+        phase_coefficients(m1[t], m2[t], pn, b->df, &coef[t * kNB]);
+        for (int i = 0; i < kNB; ++i) {
+            const double c = coef[t * kNB + i];
+            const float hi = (float)c;
+            coef_df[t * kNB + i] = make_float2(hi, (float)(c - (double)hi));
+        }
+        mass[2 * t] = M;
+        mass[2 * t + 1] = m1[t] * m2[t] / ((m1[t] + m2[t]) * (m1[t] + m2[t]));
+        iota[t] = (int32_t)t;
+    }
+
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) {
+        if (e == cudaSuccess && x != cudaSuccess) e = x;
+    };
+    const cudaStream_t s = b->stream;
+    chk(dalloc(&b->d_coef, nt * kNB));
+    chk(dalloc(&b->d_coef_df, nt * kNB));
+    chk(dalloc(&b->d_mass, 2 * nt));
+    chk(dalloc(&b->d_khi, nt));
+    chk(dalloc(&b->d_sigma2, nt));
+    chk(dalloc(&b->d_invnorm, nt));
+    chk(dalloc(&b->d_peak, nt));
+    chk(dalloc(&b->d_peaks, nt));
+    chk(dalloc(&b->d_iota, nt));
+    chk(dalloc(&b->d_strain, b->n));
+    chk(dalloc(&b->d_psd, b->nh + 1));
+    chk(dalloc(&b->d_amp, b->nh));
+    chk(dalloc(&b->d_prefix, b->nh + 1));
+    chk(dalloc(&b->d_scan, (b->nh + 1) / 2048 + 2));
+    chk(dalloc(&b->d_fa, b->n));
+    chk(dalloc(&b->d_fb, b->n));
+    chk(dalloc(&b->d_wbar, b->nh));
+    chk(dalloc(&b->d_scales, 1));
+    chk(dalloc(&b->d_trig, b->trig_cap));
+    chk(dalloc(&b->d_trig_count, 1));
+    chk(dalloc(&b->d_err, 1));
+    if (b->fused) {
+        fused_default_tiling(b->log2n, &b->n1, &b->ccols, &b->rpc);
+        b->n2 = (int)(b->n / b->n1);
+        const size_t per = (size_t)b->n * ((d.flags & CUI_STORE_BF16) ? 4 : 8);
+        b->batch = (int)std::max<int64_t>(1, std::min<int64_t>(4096, ((int64_t)1 << 30) / (int64_t)per));
+        b->batch = (int)std::min<int64_t>(b->batch, nt);
+        const int64_t na = (int64_t)(b->n1 / 2) * (b->n2 / b->ccols);
+        chk(dalloc(&b->d_basis, na * kNB));
+        chk(dalloc(&b->d_basis_df, na * kNB));
+        chk(cudaMalloc(&b->d_y, per * (size_t)b->batch));
+        b->h_kex.resize(nt);
+        for (int64_t t = 0; t < nt; ++t) {
+            b->h_kex[t] = exact_bound(coef[t * kNB], b->ccols, b->nh);
+            b->kx = std::max(b->kx, b->h_kex[t]);
+        }
+        chk(dalloc(&b->d_kex, nt));
+        chk(dalloc(&b->d_gexact, (int64_t)std::max(1, b->kx) * kNB));
+        chk(dalloc(&b->d_win, (int64_t)b->batch * std::max(1, b->nwin)));
+    } else {
+        const size_t rs = b->plain_fp64 ? sizeof(double2) : sizeof(float2);
+        chk(cudaMalloc(&b->d_dS, rs * b->nh));
+        chk(cudaMalloc(&b->d_h, rs * b->nh));
+        chk(cudaMalloc(&b->d_qa, rs * b->n));
+        chk(cudaMalloc(&b->d_qb, rs * b->n));
+        chk(dalloc(&b->d_acc, 1));
+        chk(dalloc(&b->d_pwin, std::max(1, b->nwin)));
+    }
+    if (e != cudaSuccess) {
+        release(b);
+        delete b;
+        return cuda_fail(e, "cui_bank_create");
+    }
+    chk(cudaMemcpyAsync(b->d_coef, coef.data(), sizeof(double) * nt * kNB, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(b->d_coef_df, coef_df.data(), sizeof(float2) * nt * kNB, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(b->d_mass, mass.data(), sizeof(double) * 2 * nt, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(b->d_khi, b->h_khi.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(b->d_iota, iota.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
+    chk(cudaMemsetAsync(b->d_peak, 0, sizeof(Slot) * nt, s));
+    chk(cudaMemsetAsync(b->d_err, 0, sizeof(int), s));
+    chk(cudaMemsetAsync(b->d_trig_count, 0, sizeof(unsigned long long), s));
+    launch_amp_table(b->d_amp, b->nh, s);
+    if (b->fused) {
+        chk(cudaMemsetAsync(b->d_win, 0, sizeof(Slot) * (size_t)b->batch * std::max(1, b->nwin), s));
+        launch_basis_table(b->d_basis, b->d_basis_df, b->n1, b->n2, b->ccols, s);
+        chk(cudaMemcpyAsync(b->d_kex, b->h_kex.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
+        launch_exact_table(b->d_gexact, b->kx, s);
+        fused_set_consts(make_deriv_consts(), s);
+    } else {
+        chk(cudaMemsetAsync(b->d_pwin, 0, sizeof(Slot) * std::max(1, b->nwin), s));
+    }
+    chk(cudaGetLastError());
+    // the host vectors above are pageable: wait for their copies before they go
+    chk(cudaStreamSynchronize(s));
+    if (e != cudaSuccess) {
+        release(b);
+        delete b;
+        return cuda_fail(e, "cui_bank_create");
+    }
+    *out = b;
+    return CUI_OK;
+}
+
+extern "C" void cui_bank_destroy(cui_bank b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    release(b);
+    delete b;
+}
+
+extern "C" cui_status cui_segment_upload(cui_bank b, const double *strain, int64_t n, const double *psd,
+                                         int64_t n_psd, int on_device)
+{
+    if (!b) return fail(CUI_ERR_ARG, "bank is NULL");
+    if (!strain || !psd) return fail(CUI_ERR_ARG, "strain and psd must be non-NULL");
+    if (n != b->n) return fail(CUI_ERR_ARG, "n = %lld differs from the bank's %lld", (long long)n, (long long)b->n);
+    if (n_psd != b->nh + 1) return fail(CUI_ERR_ARG, "n_psd must be N/2 + 1 = %lld", (long long)(b->nh + 1));
+    if (!on_device) {
+        for (int64_t k = b->k_low; k < b->nh; ++k)
+            if (!(psd[k] > 0) || !std::isfinite(psd[k]))
+                return fail(CUI_ERR_ARG, "psd[%lld] must be finite and > 0 in the band", (long long)k);
+    }
+    const cudaStream_t s = b->stream;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CUI_TRY(cudaMemcpyAsync(b->d_strain, strain, sizeof(double) * b->n, kind, s), "strain copy");
+    CUI_TRY(cudaMemcpyAsync(b->d_psd, psd, sizeof(double) * (b->nh + 1), kind, s), "psd copy");
+    Span span(b, 0);
+    launch_real_to_complex(b->d_strain, b->d_fa, b->n, s);
+    double2 *X = nullptr;
+    launch_fft_passes_f64(b->d_fa, b->d_fb, b->log2n, -1, s, &X);
+    launch_weighted_data(X, b->d_psd, b->d_amp, b->n, b->k_low, b->desc.sample_rate, b->d_scales, b->d_wbar,
+                         b->d_dS, b->plain_fp64, s);
+    launch_prefix(b->d_psd, b->d_amp, b->n, b->k_low, b->d_prefix, b->d_scan, s);
+    launch_template_norm(b->d_prefix, b->d_khi, b->nt, b->desc.sample_rate, b->n, b->d_scales, b->d_sigma2,
+                         b->d_invnorm, s);
+    CUI_TRY(cudaGetLastError(), "cui_segment_upload");
+    b->have_segment = true;
+    return CUI_OK;
+}
+
+static FusedArgs fused_args(cui_bank b, const int32_t *order, int64_t base)
+{
+    FusedArgs a;
+    a.wbar = b->d_wbar;
+    a.coef = b->d_coef;
+    a.coef_df = b->d_coef_df;
+    a.basis = b->d_basis;
+    a.basis_df = b->d_basis_df;
+    a.khi = b->d_khi;
+    a.kex = b->d_kex;
+    a.gexact = b->d_gexact;
+    a.invnorm = b->d_invnorm;
+    a.order = order;
+    a.base = base;
+    a.ywork = b->d_y;
+    a.peak = b->d_peak;
+    a.win = b->d_win;
+    a.err = b->d_err;
+    a.n = b->n;
+    a.log2n = b->log2n;
+    a.n1 = b->n1;
+    a.n2 = b->n2;
+    a.ccols = b->ccols;
+    a.rpc = b->rpc;
+    a.k_low = b->k_low;
+    a.lo = b->desc.valid_lo;
+    a.hi = b->desc.valid_hi;
+    a.window = b->desc.window;
+    a.nwin = b->nwin;
+    a.thr2 = (float)(b->desc.snr_threshold * b->desc.snr_threshold);
+    a.df = (b->desc.flags & CUI_PSI_DF) != 0;
+    a.bf16 = (b->desc.flags & CUI_STORE_BF16) != 0;
+    return a;
+}
+
+extern "C" cui_status cui_filter_bank(cui_bank b, const int32_t *order, int64_t count, cui_peak *peaks_dev)
+{
+    if (!b) return fail(CUI_ERR_ARG, "bank is NULL");
+    if (!b->have_segment) return fail(CUI_ERR_STATE, "no segment uploaded");
+    if (count < 0 || count > b->nt) return fail(CUI_ERR_ARG, "count must be in [0, n_templates]");
+    if (!order && count != b->nt) return fail(CUI_ERR_ARG, "order == NULL requires count == n_templates");
+    const cudaStream_t s = b->stream;
+    const int32_t *d_ord = b->d_iota;
+    if (order) {
+        std::vector<uint8_t> seen(b->nt, 0);
+        for (int64_t i = 0; i < count; ++i) {
+            if (order[i] < 0 || order[i] >= b->nt)
+                return fail(CUI_ERR_ARG, "order[%lld] = %d out of range", (long long)i, order[i]);
+            if (seen[order[i]]++) return fail(CUI_ERR_ARG, "order lists template %d twice", order[i]);
+        }
+        if (count > b->order_cap) {
+            if (b->d_order) cudaFree(b->d_order);
+            b->d_order = nullptr;
+            b->order_cap = 0;
+            CUI_TRY(dalloc(&b->d_order, count), "order buffer");
+            b->order_cap = count;
+        }
+        if (count) CUI_TRY(cudaMemcpyAsync(b->d_order, order, sizeof(int32_t) * count, cudaMemcpyHostToDevice, s),
+                           "order copy");
+        d_ord = b->d_order;
+    }
+    CUI_TRY(cudaMemsetAsync(b->d_trig_count, 0, sizeof(unsigned long long), s), "trigger reset");
+    cui_peak *pout = peaks_dev ? peaks_dev : b->d_peaks;
+    FinalizeArgs fa;
+    fa.order = d_ord;
+    fa.peak = b->d_peak;
+    fa.nwin = b->nwin;
+    fa.lo = b->desc.valid_lo;
+    fa.window = b->desc.window;
+    fa.peaks_out = pout;
+    fa.trig = b->d_trig;
+    fa.trig_cap = b->trig_cap;
+    fa.trig_count = b->d_trig_count;
+    if (b->fused) {
+        fa.win = b->d_win;
+        for (int64_t base = 0; base < count; base += b->batch) {
+            const int bc = (int)std::min<int64_t>(b->batch, count - base);
+            FusedArgs a = fused_args(b, d_ord, base);
+            {
+                Span sp(b, 1);
+                CUI_TRY(launch_pass1(a, bc, s), "fused pass 1");
+            }
+            {
+                Span sp(b, 2);
+                CUI_TRY(launch_pass2(a, bc, s), "fused pass 2");
+            }
+            fa.base = base;
+            fa.count = bc;
+            Span sp(b, 3);
+            CUI_TRY(launch_finalize(fa, s), "finalize");
+        }
+    } else {
+        PlainArgs a;
+        a.mass = b->d_mass;
+        a.khi = b->d_khi;
+        a.amp = b->d_amp;
+        a.psd = b->d_psd;
+        a.dS = b->d_dS;
+        a.scales = b->d_scales;
+        a.h = b->d_h;
+        a.qa = b->d_qa;
+        a.qb = b->d_qb;
+        a.acc = b->d_acc;
+        a.peak = b->d_peak;
+        a.win = b->d_pwin;
+        a.err = b->d_err;
+        a.n = b->n;
+        a.log2n = b->log2n;
+        a.pn_x2 = b->desc.pn_order_x2;
+        a.k_low = b->k_low;
+        a.fs = b->desc.sample_rate;
+        a.lo = b->desc.valid_lo;
+        a.hi = b->desc.valid_hi;
+        a.window = b->desc.window;
+        a.nwin = b->nwin;
+        a.thr2 = (float)(b->desc.snr_threshold * b->desc.snr_threshold);
+        a.fp64 = b->plain_fp64;
+        fa.win = b->d_pwin;
+        fa.count = 1;
+        for (int64_t pos = 0; pos < count; ++pos) {
+            const int t = order ? order[pos] : (int)pos;
+            Span sp(b, 4);
+            CUI_TRY(launch_plain_template(a, t, s), "plain filter");
+            fa.base = pos;
+            CUI_TRY(launch_finalize(fa, s), "finalize");
+        }
+    }
+    b->have_peaks = peaks_dev == nullptr;
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_trace_enable(cui_bank b, int on)
+{
+    if (!b) return fail(CUI_ERR_ARG, "bank is NULL");
+    b->trace = on != 0;
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_trace_read(cui_bank b, cui_trace_stat *host_out, int64_t capacity, int64_t *n)
+{
+    if (!b || !n || capacity < 0 || (capacity > 0 && !host_out)) return fail(CUI_ERR_ARG, "bad arguments");
+    CUI_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    cui_trace_stat st[kNGroups];
+    std::memset(st, 0, sizeof st);
+    for (int g = 0; g < kNGroups; ++g) std::snprintf(st[g].name, sizeof st[g].name, "%s", kGroups[g]);
+    cudaError_t e = cudaSuccess;
+    for (auto &m : b->marks) {
+        float ms = 0.f;
+        cudaError_t x = cudaEventElapsedTime(&ms, m.a, m.b);
+        if (x != cudaSuccess && e == cudaSuccess) e = x;
+        st[m.group].ms += ms;
+        st[m.group].calls += 1;
+        st[m.group].launches += m.launches;
+        b->pool.push_back(m.a);
+        b->pool.push_back(m.b);
+    }
+    b->marks.clear();
+    if (e != cudaSuccess) return cuda_fail(e, "trace events");
+    int64_t k = 0;
+    for (int g = 0; g < kNGroups; ++g)
+        if (st[g].calls) {
+            if (k < capacity) host_out[k] = st[g];
+            ++k;
+        }
+    *n = k;
+    return CUI_OK;
+}
+
+static cui_status sync_and_check(cui_bank b)
+{
+    CUI_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    int err = 0;
+    CUI_TRY(cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error word");
+    if (err) {
+        cudaMemset(b->d_err, 0, sizeof(int));
+        return fail(CUI_ERR_TIMEOUT, "a bounded device wait gave up (code %d)", err);
+    }
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_peaks(cui_bank b, cui_peak *host_out, int64_t count)
+{
+    if (!b || !host_out) return fail(CUI_ERR_ARG, "bank and host_out must be non-NULL");
+    if (count < 0 || count > b->nt) return fail(CUI_ERR_ARG, "count must be in [0, n_templates]");
+    if (!b->have_peaks) return fail(CUI_ERR_STATE, "no filter call kept its peaks in the handle");
+    cui_status st = sync_and_check(b);
+    if (st != CUI_OK) return st;
+    CUI_TRY(cudaMemcpy(host_out, b->d_peaks, sizeof(cui_peak) * count, cudaMemcpyDeviceToHost), "peaks copy");
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_triggers(cui_bank b, cui_trigger *host_out, int64_t capacity, int64_t *n_total)
+{
+    if (!b || !n_total) return fail(CUI_ERR_ARG, "bank and n_total must be non-NULL");
+    if (capacity < 0 || (capacity > 0 && !host_out)) return fail(CUI_ERR_ARG, "bad capacity / host_out");
+    cui_status st = sync_and_check(b);
+    unsigned long long cnt = 0;
+    CUI_TRY(cudaMemcpy(&cnt, b->d_trig_count, sizeof cnt, cudaMemcpyDeviceToHost), "trigger count");
+    *n_total = (int64_t)cnt;
+    if (st != CUI_OK) return st;
+    const int64_t have = std::min<int64_t>((int64_t)cnt, b->trig_cap);
+    std::vector<cui_trigger> tmp(have);
+    if (have) CUI_TRY(cudaMemcpy(tmp.data(), b->d_trig, sizeof(cui_trigger) * have, cudaMemcpyDeviceToHost),
+                      "trigger copy");
+    std::sort(tmp.begin(), tmp.end(), [](const cui_trigger &x, const cui_trigger &y) {
+        return x.tmpl != y.tmpl ? x.tmpl < y.tmpl : x.sample < y.sample;
+    });
+    const int64_t nout = std::min<int64_t>(have, capacity);
+    if (nout) std::memcpy(host_out, tmp.data(), sizeof(cui_trigger) * nout);
+    if ((int64_t)cnt > b->trig_cap)
+        return fail(CUI_ERR_OVERFLOW, "%llu triggers exceed the device buffer of %lld (only those were kept)", cnt,
+                    (long long)b->trig_cap);
+    if ((int64_t)cnt > capacity)
+        return fail(CUI_ERR_OVERFLOW, "%llu triggers exceed capacity %lld", cnt, (long long)capacity);
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_bank_sigma(cui_bank b, double *host_sigma)
+{
+    if (!b || !host_sigma) return fail(CUI_ERR_ARG, "bank and host_sigma must be non-NULL");
+    if (!b->have_segment) return fail(CUI_ERR_STATE, "no segment uploaded");
+    CUI_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    CUI_TRY(cudaMemcpy(host_sigma, b->d_sigma2, sizeof(double) * b->nt, cudaMemcpyDeviceToHost), "sigma copy");
+    for (int64_t t = 0; t < b->nt; ++t) host_sigma[t] = std::sqrt(host_sigma[t]);
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_bank_template(cui_bank b, int64_t t, float *out_dev)
+{
+    if (!b || !out_dev) return fail(CUI_ERR_ARG, "bank and out_dev must be non-NULL");
+    if (t < 0 || t >= b->nt) return fail(CUI_ERR_ARG, "template index out of range");
+    if (!fused_supported(b->log2n))
+        return fail(CUI_ERR_ARG, "template read-out needs the fused path's sizes (2^12 <= N <= 2^22)");
+    if (!b->fused) {
+        // anchors for the read-out are built on first use for plain-path banks
+        if (!b->d_basis) {
+            fused_default_tiling(b->log2n, &b->n1, &b->ccols, &b->rpc);
+            b->n2 = (int)(b->n / b->n1);
+            const int64_t na = (int64_t)(b->n1 / 2) * (b->n2 / b->ccols);
+            CUI_TRY(dalloc(&b->d_basis, na * kNB), "basis table");
+            CUI_TRY(dalloc(&b->d_basis_df, na * kNB), "basis table");
+            launch_basis_table(b->d_basis, b->d_basis_df, b->n1, b->n2, b->ccols, b->stream);
+            std::vector<double> c(kNB);
+            b->h_kex.assign(b->nt, 0);
+            for (int64_t i = 0; i < b->nt; ++i) {
+                CUI_TRY(cudaMemcpy(c.data(), b->d_coef + i * kNB, sizeof(double) * kNB, cudaMemcpyDeviceToHost),
+                        "coefficients");
+                b->h_kex[i] = exact_bound(c[0], b->ccols, b->nh);
+                b->kx = std::max(b->kx, b->h_kex[i]);
+            }
+            CUI_TRY(dalloc(&b->d_kex, b->nt), "exact bounds");
+            CUI_TRY(dalloc(&b->d_gexact, (int64_t)std::max(1, b->kx) * kNB), "exact table");
+            CUI_TRY(cudaMemcpy(b->d_kex, b->h_kex.data(), sizeof(int32_t) * b->nt, cudaMemcpyHostToDevice),
+                    "exact bounds");
+            launch_exact_table(b->d_gexact, b->kx, b->stream);
+            fused_set_consts(make_deriv_consts(), b->stream);
+        }
+    }
+    FusedArgs a = fused_args(b, b->d_iota, 0);
+    const double dfac = std::pow(b->df, -7.0 / 6.0);
+    CUI_TRY(launch_template_out(a, (int)t, b->d_amp, dfac, (float2 *)out_dev, b->stream), "template read-out");
+    return CUI_OK;
+}

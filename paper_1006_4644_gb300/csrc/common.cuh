@@ -1,0 +1,212 @@
+// Device helpers shared by the library's kernels: complex arithmetic,
+// in-register DFTs of radix 2/4/8/16, double-float (FP32 pair) arithmetic and
+// the 16-byte "best sample" slot updated with a 128-bit compare-and-swap.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define CUI_HD __host__ __device__ __forceinline__
+
+namespace cui {
+
+// ---------------------------------------------------------------- complex ---
+template <typename R> struct cpx;
+template <> struct cpx<float> { using T = float2; };
+template <> struct cpx<double> { using T = double2; };
+template <typename R> using cpx_t = typename cpx<R>::T;
+
+CUI_HD float2 mk(float x, float y) { return make_float2(x, y); }
+CUI_HD double2 mk(double x, double y) { return make_double2(x, y); }
+CUI_HD float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+CUI_HD float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+CUI_HD double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+CUI_HD double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+template <typename C> CUI_HD C cmul(C a, C b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename C> CUI_HD C cmulc(C a, C b) { return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); } // a * conj(b)
+template <typename C, typename R> CUI_HD C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
+// multiply by sign * i  (i for SIGN = +1, -i for SIGN = -1)
+template <int SIGN, typename C> CUI_HD C mul_si(C a) { return SIGN > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x); }
+
+// ------------------------------------------------------ in-register DFTs ---
+// y_k = sum_r v_r exp(SIGN 2 pi i r k / R), in place, natural order.
+template <int SIGN, typename C> CUI_HD void dft2(C &a, C &b)
+{
+    C t = a - b;
+    a = a + b;
+    b = t;
+}
+
+template <int SIGN, typename C> CUI_HD void dft4(C &v0, C &v1, C &v2, C &v3)
+{
+    C a0 = v0 + v2, a1 = v0 - v2, a2 = v1 + v3, a3 = mul_si<SIGN>(v1 - v3);
+    v0 = a0 + a2;
+    v2 = a0 - a2;
+    v1 = a1 + a3;
+    v3 = a1 - a3;
+}
+
+template <typename R> struct k16 {
+    static constexpr R c1 = R(0.92387953251128675613); // cos(pi/8)
+    static constexpr R s1 = R(0.38268343236508977173); // sin(pi/8)
+    static constexpr R r2 = R(0.70710678118654752440); // cos(pi/4)
+};
+
+// omega_8^m for m = 1, 2, 3 applied to a (SIGN-dependent direction)
+template <int SIGN, typename C, typename R> CUI_HD C w8(C a, int m)
+{
+    const R h = k16<R>::r2;
+    if (m == 1) return cmul(a, mk(h, SIGN * h));
+    if (m == 2) return mul_si<SIGN>(a);
+    return cmul(a, mk(-h, SIGN * h));
+}
+
+template <int SIGN, typename C> CUI_HD void dft8(C *v)
+{
+    using R = decltype(v[0].x);
+    // r = r1 + 2 r2: DFT4 over r2 for r1 = 0, 1; twiddle w8^(r1 k2); DFT2 over r1.
+    dft4<SIGN>(v[0], v[2], v[4], v[6]);
+    dft4<SIGN>(v[1], v[3], v[5], v[7]);
+    v[3] = w8<SIGN, C, R>(v[3], 1);
+    v[5] = w8<SIGN, C, R>(v[5], 2);
+    v[7] = w8<SIGN, C, R>(v[7], 3);
+    // now a[r1][k2] sits at v[r1 + 2 k2]; output y[k2 + 4 k1] = a[0][k2] +/- a[1][k2]
+    C y[8];
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+        y[k2] = v[2 * k2] + v[2 * k2 + 1];
+        y[k2 + 4] = v[2 * k2] - v[2 * k2 + 1];
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = y[i];
+}
+
+template <int SIGN, typename C> CUI_HD void dft16(C *v)
+{
+    using R = decltype(v[0].x);
+    // r = r1 + 4 r2: DFT4 over r2 for each r1, twiddle w16^(r1 k2), DFT4 over r1.
+#pragma unroll
+    for (int r1 = 0; r1 < 4; ++r1) dft4<SIGN>(v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12]);
+    // a[r1][k2] at v[r1 + 4 k2]
+    const R c1 = k16<R>::c1, s1 = k16<R>::s1, h = k16<R>::r2;
+    // w16^m, m = r1 * k2 in {1,2,3,4,6,9}
+    v[5] = cmul(v[5], mk(c1, SIGN * s1));          // r1=1,k2=1: m=1
+    v[9] = cmul(v[9], mk(h, SIGN * h));            // r1=1,k2=2: m=2
+    v[13] = cmul(v[13], mk(s1, SIGN * c1));        // r1=1,k2=3: m=3
+    v[6] = cmul(v[6], mk(h, SIGN * h));            // r1=2,k2=1: m=2
+    v[10] = mul_si<SIGN>(v[10]);                   // r1=2,k2=2: m=4
+    v[14] = cmul(v[14], mk(-h, SIGN * h));         // r1=2,k2=3: m=6
+    v[7] = cmul(v[7], mk(s1, SIGN * c1));          // r1=3,k2=1: m=3
+    v[11] = cmul(v[11], mk(-h, SIGN * h));         // r1=3,k2=2: m=6
+    v[15] = cmul(v[15], mk(-c1, -SIGN * s1));      // r1=3,k2=3: m=9
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) dft4<SIGN>(v[4 * k2], v[4 * k2 + 1], v[4 * k2 + 2], v[4 * k2 + 3]);
+    // y[k2 + 4 k1] now at v[4 k2 + k1]: transpose 4x4
+    C y[16];
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2)
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) y[k2 + 4 * k1] = v[4 * k2 + k1];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = y[i];
+}
+
+template <int R, int SIGN, typename C> CUI_HD void dft(C *v)
+{
+    if constexpr (R == 2) dft2<SIGN>(v[0], v[1]);
+    else if constexpr (R == 4) dft4<SIGN>(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 8) dft8<SIGN>(v);
+    else dft16<SIGN>(v);
+}
+
+// ---------------------------------------------- double-float arithmetic ---
+// Error-free transformations (Knuth's two-sum, FMA two-product; Dekker 1971)
+// on FP32 pairs hi + lo, with intrinsics so no operation is contracted or
+// reassociated.
+struct df { float hi, lo; };
+
+__device__ __forceinline__ df two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_add(df a, df b)
+{
+    df s = two_sum(a.hi, b.hi);
+    df t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_mul(df a, df b)
+{
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return quick_two_sum(p, e);
+}
+
+// ------------------------------------------------------ best-sample slot ---
+// 16 bytes: key = (float bits of rho^2) << 32 | (0xFFFFFFFF - sample), so the
+// largest key is the largest rho^2 and, among equal rho^2, the lowest sample;
+// then the phase of z at that sample.  key == 0 means empty.
+struct __align__(16) Slot {
+    unsigned long long key;
+    unsigned int phase_bits;
+    unsigned int pad;
+};
+
+__device__ __forceinline__ unsigned long long make_key(float rho2, uint32_t sample)
+{
+    return ((unsigned long long)__float_as_uint(rho2) << 32) | (unsigned long long)(0xFFFFFFFFu - sample);
+}
+
+// Raise the slot to (key, phase) if key is larger.  Lock-free: each failed
+// CAS means another thread stored a larger key, so the loop ends after at most
+// as many rounds as there are competing writers; the bound only guards
+// against a logic error and is reported through *err.
+__device__ __forceinline__ void slot_max(Slot *s, unsigned long long key, float phase, int *err)
+{
+    unsigned long long cur_lo = *(volatile unsigned long long *)&s->key;
+    unsigned long long cur_hi = *(volatile unsigned long long *)&s->phase_bits;
+    const unsigned long long new_hi = (unsigned long long)__float_as_uint(phase);
+    for (int it = 0; it < (1 << 20); ++it) {
+        if (cur_lo >= key) return;
+        unsigned long long old_lo, old_hi;
+        asm volatile("{\n\t.reg .b128 d, c, n;\n\t"
+                     "mov.b128 c, {%2, %3};\n\t"
+                     "mov.b128 n, {%4, %5};\n\t"
+                     "atom.global.cas.b128 d, [%6], c, n;\n\t"
+                     "mov.b128 {%0, %1}, d;\n\t}"
+                     : "=l"(old_lo), "=l"(old_hi)
+                     : "l"(cur_lo), "l"(cur_hi), "l"(key), "l"(new_hi), "l"(s)
+                     : "memory");
+        if (old_lo == cur_lo && old_hi == cur_hi) return;
+        cur_lo = old_lo;
+        cur_hi = old_hi;
+    }
+    atomicOr(err, 2);
+}
+
+// Warp-wide maximum of (key, zr, zi) by key.
+__device__ __forceinline__ void warp_max_key(unsigned long long &key, float &zr, float &zi)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, off);
+        float r2 = __shfl_xor_sync(0xffffffffu, zr, off);
+        float i2 = __shfl_xor_sync(0xffffffffu, zi, off);
+        if (k2 > key) { key = k2; zr = r2; zi = i2; }
+    }
+}
+
+} // namespace cui

@@ -1,0 +1,389 @@
+// Segment preparation: the FP64 data spectrum d~ (eq:matchedfilter's X(f)),
+// the noise-weighted data the filters read, per-template sigma^2 from prefix
+// sums, and the template-independent tables (amplitude law, anchor basis).
+// Also the generic multi-pass Stockham FFT over global memory that the
+// segment transform and the per-template plain path use.
+#include <cstdio>
+
+#include "internal.h"
+
+namespace cui {
+
+// ------------------------------------------------ Stockham global passes ---
+template <typename Rl> __device__ __forceinline__ cpx_t<Rl> unit_turn(int64_t m, int64_t d, int sign);
+template <> __device__ __forceinline__ double2 unit_turn<double>(int64_t m, int64_t d, int sign)
+{
+    double s, c;
+    sincospi(2.0 * (double)m / (double)d, &s, &c);
+    return make_double2(c, sign * s);
+}
+template <> __device__ __forceinline__ float2 unit_turn<float>(int64_t m, int64_t d, int sign)
+{
+    float s, c;
+    sincospif(2.0f * (float)m / (float)d, &s, &c);
+    return make_float2(c, sign * s);
+}
+
+// One radix-R Stockham stage over a length-L transform whose sub-transforms
+// of size Ns are done: task j reads in[j + r L/R], applies the twiddles
+// exp(SIGN 2 pi i (j mod Ns) r / (Ns R)), an R-point DFT, and writes
+// out[(j / Ns) Ns R + j mod Ns + r Ns].
+template <typename Rl, int R, int SIGN>
+__global__ void __launch_bounds__(256) k_stockham(const cpx_t<Rl> *__restrict__ in, cpx_t<Rl> *__restrict__ out,
+                                                  int64_t L, int64_t Ns)
+{
+    using C = cpx_t<Rl>;
+    const int64_t q = L / R;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= q) return;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[j + r * q];
+    const int64_t jm = j & (Ns - 1);
+    if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], unit_turn<Rl>(jm * r, Ns * R, SIGN));
+    }
+    dft<R, SIGN>(v);
+    const int64_t idx = (j / Ns) * Ns * R + jm;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[idx + r * Ns] = v[r];
+}
+
+template <typename Rl, int SIGN> static void stage(const cpx_t<Rl> *in, cpx_t<Rl> *out, int64_t L, int64_t Ns, int R,
+                                                  cudaStream_t s)
+{
+    const int64_t q = L / R;
+    const unsigned blocks = (unsigned)((q + 255) / 256);
+    switch (R) {
+    case 2: k_stockham<Rl, 2, SIGN><<<blocks, 256, 0, s>>>(in, out, L, Ns); break;
+    case 4: k_stockham<Rl, 4, SIGN><<<blocks, 256, 0, s>>>(in, out, L, Ns); break;
+    case 8: k_stockham<Rl, 8, SIGN><<<blocks, 256, 0, s>>>(in, out, L, Ns); break;
+    default: k_stockham<Rl, 16, SIGN><<<blocks, 256, 0, s>>>(in, out, L, Ns); break;
+    }
+    launched();
+}
+
+// Full transform of length 2^log2n: one small-radix stage (if log2n is not a
+// multiple of 4) then radix-16 stages, ping-ponging between a and b.
+template <typename Rl>
+static void fft_passes(cpx_t<Rl> *a, cpx_t<Rl> *b, int log2n, int sign, cudaStream_t s, cpx_t<Rl> **result)
+{
+    const int64_t L = int64_t(1) << log2n;
+    int64_t Ns = 1;
+    cpx_t<Rl> *src = a, *dst = b;
+    int rem = log2n % 4;
+    int left = log2n;
+    while (left > 0) {
+        int lr = rem ? rem : 4;
+        rem = 0;
+        int R = 1 << lr;
+        if (sign > 0) stage<Rl, +1>(src, dst, L, Ns, R, s);
+        else stage<Rl, -1>(src, dst, L, Ns, R, s);
+        Ns *= R;
+        left -= lr;
+        cpx_t<Rl> *t = src;
+        src = dst;
+        dst = t;
+    }
+    *result = src;
+}
+
+void launch_fft_passes_f64(double2 *a, double2 *b, int log2n, int sign, cudaStream_t s, double2 **result)
+{
+    fft_passes<double>(a, b, log2n, sign, s, result);
+}
+void launch_fft_passes_f32(float2 *a, float2 *b, int log2n, int sign, cudaStream_t s, float2 **result)
+{
+    fft_passes<float>(a, b, log2n, sign, s, result);
+}
+
+// -------------------------------------------------------- segment inputs ---
+__global__ void k_real_to_complex(const double *__restrict__ d, double2 *__restrict__ out, int64_t n)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        out[j] = make_double2(d[j], 0.0);
+}
+void launch_real_to_complex(const double *d, double2 *out, int64_t n, cudaStream_t s)
+{
+    k_real_to_complex<<<1216, 256, 0, s>>>(d, out, n);
+    launched();
+}
+
+// amp_k = k^(-7/6) for k >= 1 (the Newtonian amplitude law without its
+// df^(-7/6) factor), amp_0 = 0.
+__global__ void k_amp(double *amp, int64_t nh)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nh; k += (int64_t)gridDim.x * blockDim.x)
+        amp[k] = k == 0 ? 0.0 : pow((double)k, -7.0 / 6.0);
+}
+void launch_amp_table(double *amp, int64_t nh, cudaStream_t s)
+{
+    k_amp<<<1216, 256, 0, s>>>(amp, nh);
+    launched();
+}
+
+__device__ __forceinline__ double warp_max_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Band maxima of |d~ amp / S| and |d~ / S| (non-negative doubles compare as
+// unsigned integers, so atomicMax on their bits is a floating-point max).
+__global__ void k_wmax(const double2 *__restrict__ X, const double *__restrict__ psd, const double *__restrict__ amp,
+                       int64_t nh, int k_low, double inv_fs, SegScales *sc)
+{
+    double mw = 0.0, md = 0.0;
+    for (int64_t k = k_low + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nh;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        double2 x = X[k];
+        double a = hypot(x.x, x.y) * inv_fs / psd[k];
+        md = fmax(md, a);
+        mw = fmax(mw, a * amp[k]);
+    }
+    mw = warp_max_d(mw);
+    md = warp_max_d(md);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax((unsigned long long *)&sc->max_w, (unsigned long long)__double_as_longlong(mw));
+        atomicMax((unsigned long long *)&sc->max_d, (unsigned long long)__double_as_longlong(md));
+    }
+}
+
+__device__ __forceinline__ double pow2_scale(double m)
+{
+    // a power of two that brings m into [1, 2); exact, so rho is unchanged
+    return m > 0.0 ? ldexp(1.0, -ilogb(m)) : 1.0;
+}
+
+// wbar_k = scale_w d~_k amp_k / S_k and dS_k = scale_d d~_k / S_k on the band
+// [k_low, N/2), zero below it.
+__global__ void k_wwrite(const double2 *__restrict__ X, const double *__restrict__ psd,
+                         const double *__restrict__ amp, int64_t nh, int k_low, double inv_fs, SegScales *sc,
+                         float2 *__restrict__ wbar, void *dS, bool dS_fp64)
+{
+    const double sw = pow2_scale(sc->max_w), sd = pow2_scale(sc->max_d);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->scale_w = sw;
+        sc->scale_d = sd;
+    }
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nh; k += (int64_t)gridDim.x * blockDim.x) {
+        double2 w = make_double2(0.0, 0.0);
+        if (k >= k_low) {
+            double f = inv_fs / psd[k];
+            w = make_double2(X[k].x * f, X[k].y * f);
+        }
+        wbar[k] = make_float2((float)(w.x * amp[k] * sw), (float)(w.y * amp[k] * sw));
+        if (dS) {
+            if (dS_fp64) ((double2 *)dS)[k] = make_double2(w.x * sd, w.y * sd);
+            else ((float2 *)dS)[k] = make_float2((float)(w.x * sd), (float)(w.y * sd));
+        }
+    }
+}
+
+void launch_weighted_data(const double2 *X, const double *psd, const double *amp, int64_t n, int k_low, double fs,
+                          SegScales *scales, float2 *wbar, void *dS, bool dS_fp64, cudaStream_t s)
+{
+    const int64_t nh = n / 2;
+    cudaMemsetAsync(scales, 0, sizeof(SegScales), s);
+    k_wmax<<<1216, 256, 0, s>>>(X, psd, amp, nh, k_low, 1.0 / fs, scales);
+    k_wwrite<<<1216, 256, 0, s>>>(X, psd, amp, nh, k_low, 1.0 / fs, scales, wbar, dS, dS_fp64);
+    launched(2);
+}
+
+// ------------------------------------------------------------ prefix sums ---
+// P[k] = sum_{k_low <= k' < k} amp_k'^2 / S_k', k = 0 .. N/2, in FP64.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;
+constexpr int kScanBlock = kScanThreads * kScanPer;
+
+__device__ __forceinline__ double g_term(const double *psd, const double *amp, int64_t k, int64_t nh, int k_low)
+{
+    if (k < k_low || k >= nh) return 0.0;
+    double a = amp[k];
+    return a * a / psd[k];
+}
+
+__device__ __forceinline__ double block_exclusive_scan(double v, double *sh, double *total)
+{
+    // inclusive warp scan, then scan of warp totals
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        double y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        double w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            double y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        sh[lane] = w;
+    }
+    __syncthreads();
+    double warp_off = wid ? sh[wid - 1] : 0.0;
+    *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return warp_off + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const double *psd, const double *amp, int64_t nh,
+                                                            int k_low, double *bsum)
+{
+    __shared__ double sh[32];
+    const int64_t k0 = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) s += g_term(psd, amp, k0 + i, nh, k_low);
+    double tot;
+    block_exclusive_scan(s, sh, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_offsets(double *bsum, int nb)
+{
+    __shared__ double sh[32];
+    double carry = 0.0;
+    for (int base = 0; base < nb; base += 1024) {
+        int i = base + threadIdx.x;
+        double v = i < nb ? bsum[i] : 0.0;
+        double tot;
+        double ex = block_exclusive_scan(v, sh, &tot);
+        if (i < nb) bsum[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_write(const double *psd, const double *amp, int64_t nh,
+                                                             int k_low, const double *boff, double *prefix)
+{
+    __shared__ double sh[32];
+    const int64_t k0 = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
+    double g[kScanPer];
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        g[i] = g_term(psd, amp, k0 + i, nh, k_low);
+        s += g[i];
+    }
+    double tot;
+    double run = boff[blockIdx.x] + block_exclusive_scan(s, sh, &tot);
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        if (k0 + i <= nh) prefix[k0 + i] = run;
+        run += g[i];
+    }
+}
+
+void launch_prefix(const double *psd, const double *amp, int64_t n, int k_low, double *prefix, double *work,
+                   cudaStream_t s)
+{
+    const int64_t nh = n / 2;
+    // nh + 1 outputs (P[nh] is the total)
+    const int nb = (int)((nh + 1 + kScanBlock - 1) / kScanBlock);
+    k_scan_sums<<<nb, kScanThreads, 0, s>>>(psd, amp, nh, k_low, work);
+    k_scan_offsets<<<1, 1024, 0, s>>>(work, nb);
+    k_scan_write<<<nb, kScanThreads, 0, s>>>(psd, amp, nh, k_low, work, prefix);
+    launched(3);
+}
+
+// sigma^2_t = 4 df df^(-7/3) P[k_hi(t)] (the amplitude law's df^(-7/6) factor
+// squared) and the fused path's normaliser 4 df / (scale_w^2 P[k_hi]).
+__global__ void k_tnorm(const double *prefix, const int32_t *khi, int64_t nt, int64_t nh, double df, double dfp,
+                        const SegScales *sc, double *sigma2, float *invnorm)
+{
+    const double sw = sc->scale_w;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t kh = khi[t];
+        kh = kh < 0 ? 0 : (kh > nh ? nh : kh);
+        double P = prefix[kh];
+        sigma2[t] = 4.0 * df * dfp * P;
+        invnorm[t] = P > 0.0 ? (float)(4.0 * df / (sw * sw * P)) : 0.0f;
+    }
+}
+
+void launch_template_norm(const double *prefix, const int32_t *khi, int64_t nt, double fs, int64_t n,
+                          const SegScales *scales, double *sigma2, float *invnorm, cudaStream_t s)
+{
+    const double df = fs / (double)n;
+    const double dfp = pow(df, -7.0 / 3.0);
+    const int blocks = (int)((nt + 255) / 256);
+    k_tnorm<<<blocks < 1216 ? blocks : 1216, 256, 0, s>>>(prefix, khi, nt, n / 2, df, dfp, scales, sigma2, invnorm);
+    launched();
+}
+
+// ------------------------------------------------------ anchor basis table --
+// Anchor (a, cb) sits at bin k_a = n2 a + cb C + C/2 for rows a < n1/2 and
+// column blocks cb < n2/C.  The phase of every template is a fixed linear
+// combination of nine template-independent functions of k (see bank
+// creation), tabulated here at every anchor:
+//   k^-5/3, k^-1, k^-2/3, k^-1/3, 1, ln k, k^1/3, k^1/3 ln k, k^2/3.
+__device__ __forceinline__ void basis_values(double k, double *v)
+{
+    const double q = cbrt(k), lk = log(k);
+    v[0] = 1.0 / (k * q * q);
+    v[1] = 1.0 / k;
+    v[2] = 1.0 / (q * q);
+    v[3] = 1.0 / q;
+    v[4] = 1.0;
+    v[5] = lk;
+    v[6] = q;
+    v[7] = q * lk;
+    v[8] = q * q;
+}
+
+// The same nine functions at every bin k < kx (k = 0 is never read).
+__global__ void k_exact_table(float2 *g, int kx)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kx; k += gridDim.x * blockDim.x) {
+        double v[kNB];
+        basis_values(k > 0 ? (double)k : 1.0, v);
+#pragma unroll
+        for (int i = 0; i < kNB; ++i) {
+            float hi = (float)v[i];
+            g[(int64_t)k * kNB + i] = make_float2(hi, (float)(v[i] - (double)hi));
+        }
+    }
+}
+
+void launch_exact_table(float2 *g, int kx, cudaStream_t s)
+{
+    if (kx > 0) {
+        k_exact_table<<<(kx + 255) / 256, 256, 0, s>>>(g, kx);
+        launched();
+    }
+}
+
+__global__ void k_basis(double *g, float2 *gdf, int n1, int n2, int ccols)
+{
+    const int nb = n2 / ccols;
+    const int na = (n1 / 2) * nb;
+    for (int ai = blockIdx.x * blockDim.x + threadIdx.x; ai < na; ai += gridDim.x * blockDim.x) {
+        const int a = ai / nb, cb = ai % nb;
+        const double k = (double)n2 * a + (double)cb * ccols + ccols / 2;
+        double v[kNB];
+        basis_values(k, v);
+#pragma unroll
+        for (int i = 0; i < kNB; ++i) {
+            g[(int64_t)ai * kNB + i] = v[i];
+            float hi = (float)v[i];
+            gdf[(int64_t)ai * kNB + i] = make_float2(hi, (float)(v[i] - (double)hi));
+        }
+    }
+}
+
+void launch_basis_table(double *g, float2 *g_df, int n1, int n2, int ccols, cudaStream_t s)
+{
+    const int na = (n1 / 2) * (n2 / ccols);
+    const int blocks = (na + 255) / 256;
+    k_basis<<<blocks, 256, 0, s>>>(g, g_df, n1, n2, ccols);
+    launched();
+}
+
+} // namespace cui
