@@ -57,7 +57,7 @@ typedef enum {
 } cui_status;
 
 /* desc.flags */
-#define CUI_PSI_DF      0x1u /* fused path: anchor phases in double-float (FP32 pairs) instead of FP64 */
+#define CUI_PSI_FP64    0x1u /* fused path: anchor phases in native FP64 (default: double-float FP32 pairs) */
 #define CUI_STORE_BF16  0x2u /* fused path: store the spectrum between FFT passes as bf16 pairs */
 #define CUI_PLAIN       0x4u /* per-template unfused path: generate, multiply, multi-pass FFT, detect */
 #define CUI_PLAIN_FP64  0x8u /* with CUI_PLAIN: template, product and FFT in FP64 (else FP32) */
@@ -154,6 +154,36 @@ cui_status cui_bank_sigma(cui_bank bank, double *host_sigma);
  * outside [k_lo, k_hi).  Asynchronous.  Errors: CUI_ERR_ARG, CUI_ERR_CUDA.
  * Paper: device_template_proc (Sec. "Pipeline main details"). */
 cui_status cui_bank_template(cui_bank bank, int64_t t, float *out_dev);
+
+/* Tiling of the fused path.  The correlator of length N is computed as
+ * N = n1 * n2: pass 1 runs n1-point transforms over `ccols` columns per CTA
+ * (fused with template generation), pass 2 runs n2-point transforms over
+ * `rpc` rows per CTA (fused with the peak / threshold reduction), and
+ * `batch` templates share one pass-1 / pass-2 launch pair (their spectra,
+ * batch * N complex values, live in a workspace between the passes). */
+typedef struct {
+    int32_t n1;    /* 64, 128 or 256 (subject to the kernels built for N) */
+    int32_t ccols; /* 32 or 64 */
+    int32_t rpc;   /* rows per pass-2 CTA */
+    int32_t batch; /* templates per launch pair, >= 1 */
+} cui_tuning;
+
+/* Current tiling.  Errors: CUI_ERR_ARG, CUI_ERR_STATE (per-template path). */
+cui_status cui_bank_get_tuning(cui_bank bank, cui_tuning *out);
+
+/* Select a tiling; reallocates the workspace (synchronises the stream).
+ * Errors: CUI_ERR_ARG (no kernel for that tiling at this N), CUI_ERR_STATE
+ * (per-template path), CUI_ERR_OOM, CUI_ERR_CUDA.  Results do not depend on
+ * the tiling beyond floating-point rounding. */
+cui_status cui_bank_set_tuning(cui_bank bank, const cui_tuning *tuning);
+
+/* Autotuner: time cui_filter_bank on the uploaded segment (`reps` calls per
+ * candidate, CUDA events on desc.stream) for every tiling that has kernels at
+ * this N, keep the fastest selected, and return it and its time per call.
+ * Overwrites the peaks and triggers of earlier calls.  Errors:
+ * CUI_ERR_STATE (no segment, or per-template path), CUI_ERR_ARG, CUI_ERR_CUDA.
+ * Not in the paper: its kernels had no tunable tiling. */
+cui_status cui_bank_autotune(cui_bank bank, int32_t reps, cui_tuning *best, double *best_ms);
 
 /* Tracing.  With tracing on, every call records CUDA events on desc.stream
  * around each group of kernels it launches ("segment", "pass1", "pass2",

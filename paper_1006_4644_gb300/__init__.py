@@ -19,10 +19,10 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (CUI_PLAIN, CUI_PLAIN_FP64, CUI_PSI_DF, CUI_STORE_BF16, PEAK_DTYPE, TRIGGER_DTYPE, CuiError,
+from ._lib import (CUI_PLAIN, CUI_PLAIN_FP64, CUI_PSI_FP64, CUI_STORE_BF16, PEAK_DTYPE, TRIGGER_DTYPE, CuiError,
                    cui_bank_desc)
 
-__all__ = ["Bank", "CuiError", "CUI_PSI_DF", "CUI_STORE_BF16", "CUI_PLAIN", "CUI_PLAIN_FP64", "PEAK_DTYPE",
+__all__ = ["Bank", "CuiError", "CUI_PSI_FP64", "CUI_STORE_BF16", "CUI_PLAIN", "CUI_PLAIN_FP64", "PEAK_DTYPE",
            "TRIGGER_DTYPE", "load"]
 
 load = _lib.load
@@ -127,6 +127,23 @@ class Bank:
     def template(self, t: int, out_dev):
         """Write h~_k (k = 0..N/2) of template t into a complex64 device tensor."""
         _lib.check(self._l.cui_bank_template(self._h, int(t), out_dev.data_ptr()), "cui_bank_template")
+
+    # -- tiling ----------------------------------------------------------------
+    def tuning(self) -> dict:
+        tu = _lib.cui_tuning()
+        _lib.check(self._l.cui_bank_get_tuning(self._h, C.byref(tu)), "cui_bank_get_tuning")
+        return tu.as_dict()
+
+    def set_tuning(self, n1: int, ccols: int, rpc: int, batch: int):
+        tu = _lib.cui_tuning(int(n1), int(ccols), int(rpc), int(batch))
+        _lib.check(self._l.cui_bank_set_tuning(self._h, C.byref(tu)), "cui_bank_set_tuning")
+
+    def autotune(self, reps: int = 2):
+        """Time every tiling with kernels at this N on the uploaded segment,
+        keep the fastest; returns (tiling, ms per filter call)."""
+        tu, ms = _lib.cui_tuning(), C.c_double()
+        _lib.check(self._l.cui_bank_autotune(self._h, int(reps), C.byref(tu), C.byref(ms)), "cui_bank_autotune")
+        return tu.as_dict(), ms.value
 
     def trace(self, on: bool = True):
         """Record CUDA events around every kernel group of later calls."""

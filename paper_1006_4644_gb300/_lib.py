@@ -17,7 +17,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "cui.h")
 CUI_OK, CUI_ERR_ARG, CUI_ERR_CUDA, CUI_ERR_OOM, CUI_ERR_STATE, CUI_ERR_OVERFLOW, CUI_ERR_TIMEOUT = range(7)
 STATUS_NAMES = {0: "CUI_OK", 1: "CUI_ERR_ARG", 2: "CUI_ERR_CUDA", 3: "CUI_ERR_OOM", 4: "CUI_ERR_STATE",
                 5: "CUI_ERR_OVERFLOW", 6: "CUI_ERR_TIMEOUT"}
-CUI_PSI_DF, CUI_STORE_BF16, CUI_PLAIN, CUI_PLAIN_FP64 = 0x1, 0x2, 0x4, 0x8
+CUI_PSI_FP64, CUI_STORE_BF16, CUI_PLAIN, CUI_PLAIN_FP64 = 0x1, 0x2, 0x4, 0x8
 
 
 class cui_bank_desc(C.Structure):
@@ -25,6 +25,13 @@ class cui_bank_desc(C.Structure):
                 ("sample_rate", C.c_double), ("n", C.c_int64), ("flags", C.c_uint32), ("reserved1", C.c_uint32),
                 ("snr_threshold", C.c_double), ("window", C.c_int64), ("valid_lo", C.c_int64),
                 ("valid_hi", C.c_int64), ("trigger_capacity", C.c_int64), ("stream", C.c_void_p)]
+
+
+class cui_tuning(C.Structure):
+    _fields_ = [("n1", C.c_int32), ("ccols", C.c_int32), ("rpc", C.c_int32), ("batch", C.c_int32)]
+
+    def as_dict(self):
+        return {"n1": self.n1, "ccols": self.ccols, "rpc": self.rpc, "batch": self.batch}
 
 
 class cui_trace_stat(C.Structure):
@@ -61,13 +68,17 @@ def load():
     lib.cui_triggers.argtypes = [vp, vp, C.c_int64, C.POINTER(C.c_int64)]
     lib.cui_bank_sigma.argtypes = [vp, vp]
     lib.cui_bank_template.argtypes = [vp, C.c_int64, vp]
+    lib.cui_bank_get_tuning.argtypes = [vp, C.POINTER(cui_tuning)]
+    lib.cui_bank_set_tuning.argtypes = [vp, C.POINTER(cui_tuning)]
+    lib.cui_bank_autotune.argtypes = [vp, C.c_int32, C.POINTER(cui_tuning), C.POINTER(C.c_double)]
     lib.cui_trace_enable.argtypes = [vp, C.c_int]
     lib.cui_trace_read.argtypes = [vp, C.POINTER(cui_trace_stat), C.c_int64, C.POINTER(C.c_int64)]
     lib.cui_bank_destroy.argtypes = [vp]
     lib.cui_bank_destroy.restype = None
     lib.cui_last_error.restype = C.c_char_p
     for name in ("cui_bank_create", "cui_segment_upload", "cui_filter_bank", "cui_peaks", "cui_triggers",
-                 "cui_bank_sigma", "cui_bank_template", "cui_trace_enable", "cui_trace_read"):
+                 "cui_bank_sigma", "cui_bank_template", "cui_trace_enable", "cui_trace_read",
+                 "cui_bank_get_tuning", "cui_bank_set_tuning", "cui_bank_autotune"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib

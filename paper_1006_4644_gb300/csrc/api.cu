@@ -165,6 +165,7 @@ struct cui_bank_s {
     float2 *d_wbar = nullptr;
     void *d_dS = nullptr;
     SegScales *d_scales = nullptr;
+    Twiddles tw = {nullptr, nullptr, nullptr, nullptr, 0, 0};
     // fused
     int n1 = 0, n2 = 0, ccols = 0, rpc = 0, batch = 0;
     double *d_basis = nullptr;
@@ -172,6 +173,7 @@ struct cui_bank_s {
     int32_t *d_kex = nullptr;
     float2 *d_gexact = nullptr;
     std::vector<int32_t> h_kex;
+    std::vector<double> h_c0; // leading phase coefficient of every template
     int kx = 0;
     void *d_y = nullptr;
     Slot *d_win = nullptr;
@@ -247,6 +249,7 @@ static void release(cui_bank b)
 {
     void *ptrs[] = {b->d_coef, b->d_coef_df, b->d_mass, b->d_khi, b->d_sigma2, b->d_invnorm, b->d_peak, b->d_peaks,
                     b->d_iota, b->d_strain, b->d_psd, b->d_amp, b->d_prefix, b->d_scan, b->d_fa, b->d_fb,
+                    b->tw.lo64, b->tw.hi64, b->tw.lo32, b->tw.hi32,
                     b->d_wbar, b->d_dS, b->d_scales, b->d_basis, b->d_basis_df, b->d_kex, b->d_gexact, b->d_y,
                     b->d_win, b->d_h, b->d_qa, b->d_qb, b->d_acc, b->d_pwin, b->d_trig, b->d_trig_count, b->d_err,
                     b->d_order};
@@ -260,6 +263,63 @@ static void release(cui_bank b)
 }
 
 extern "C" const char *cui_last_error(void) { return g_err.c_str(); }
+
+// Anchor basis table, per-template exact-phase bounds and the per-bin exact
+// table for a tiling (n1 rows, ccols columns per pass-1 CTA).  Synchronous.
+static cudaError_t build_phase_tables(cui_bank b, int n1, int ccols)
+{
+    const cudaStream_t s = b->stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    for (void *p : {(void *)b->d_basis, (void *)b->d_basis_df, (void *)b->d_kex, (void *)b->d_gexact})
+        if (p) cudaFree(p);
+    b->d_basis = nullptr;
+    b->d_basis_df = nullptr;
+    b->d_kex = nullptr;
+    b->d_gexact = nullptr;
+    const int n2 = (int)(b->n / n1);
+    const int64_t na = (int64_t)(n1 / 2) * (n2 / ccols);
+    b->h_kex.resize(b->nt);
+    b->kx = 0;
+    for (int64_t t = 0; t < b->nt; ++t) {
+        b->h_kex[t] = exact_bound(b->h_c0[t], ccols, b->nh);
+        b->kx = std::max(b->kx, b->h_kex[t]);
+    }
+    if ((e = dalloc(&b->d_basis, na * kNB)) != cudaSuccess) return e;
+    if ((e = dalloc(&b->d_basis_df, na * kNB)) != cudaSuccess) return e;
+    if ((e = dalloc(&b->d_kex, b->nt)) != cudaSuccess) return e;
+    if ((e = dalloc(&b->d_gexact, (int64_t)std::max(1, b->kx) * kNB)) != cudaSuccess) return e;
+    launch_basis_table(b->d_basis, b->d_basis_df, n1, n2, ccols, s);
+    launch_exact_table(b->d_gexact, b->kx, s);
+    fused_set_consts(make_deriv_consts(), s);
+    e = cudaMemcpyAsync(b->d_kex, b->h_kex.data(), sizeof(int32_t) * b->nt, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+// Select a tiling of the fused path and (re)allocate what depends on it.
+static cudaError_t configure_fused(cui_bank b, const cui_tuning &tu)
+{
+    if (!fused_tiling_ok(b->log2n, tu.n1, tu.ccols, tu.rpc) || tu.batch < 1) return cudaErrorInvalidValue;
+    const cudaStream_t s = b->stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (b->d_y) cudaFree(b->d_y);
+    if (b->d_win) cudaFree(b->d_win);
+    b->d_y = nullptr;
+    b->d_win = nullptr;
+    b->n1 = tu.n1;
+    b->n2 = (int)(b->n / tu.n1);
+    b->ccols = tu.ccols;
+    b->rpc = tu.rpc;
+    b->batch = (int)std::min<int64_t>(tu.batch, b->nt);
+    const size_t per = (size_t)b->n * ((b->desc.flags & CUI_STORE_BF16) ? 4 : 8);
+    if ((e = cudaMalloc(&b->d_y, per * (size_t)b->batch)) != cudaSuccess) return e;
+    if ((e = dalloc(&b->d_win, (int64_t)b->batch * std::max(1, b->nwin))) != cudaSuccess) return e;
+    e = cudaMemsetAsync(b->d_win, 0, sizeof(Slot) * (size_t)b->batch * std::max(1, b->nwin), s);
+    if (e != cudaSuccess) return e;
+    return build_phase_tables(b, tu.n1, tu.ccols);
+}
 
 extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m1, const double *m2,
                                       int64_t n_templates, cui_bank *out)
@@ -279,7 +339,7 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
         return fail(CUI_ERR_ARG, "need 0 <= valid_lo <= valid_hi <= n");
     if (!std::isfinite(d.snr_threshold) || d.snr_threshold < 0) return fail(CUI_ERR_ARG, "snr_threshold must be >= 0");
     if (d.trigger_capacity < 0) return fail(CUI_ERR_ARG, "trigger_capacity must be >= 0");
-    if (d.flags & ~(CUI_PSI_DF | CUI_STORE_BF16 | CUI_PLAIN | CUI_PLAIN_FP64)) return fail(CUI_ERR_ARG, "unknown flags");
+    if (d.flags & ~(CUI_PSI_FP64 | CUI_STORE_BF16 | CUI_PLAIN | CUI_PLAIN_FP64)) return fail(CUI_ERR_ARG, "unknown flags");
     if (n_templates < 1 || n_templates > (int64_t(1) << 31) - 1) return fail(CUI_ERR_ARG, "n_templates out of range");
     for (int64_t i = 0; i < n_templates; ++i)
         if (!(m1[i] > 0) || !(m2[i] > 0) || !std::isfinite(m1[i]) || !std::isfinite(m2[i]))
@@ -345,27 +405,19 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     chk(dalloc(&b->d_fb, b->n));
     chk(dalloc(&b->d_wbar, b->nh));
     chk(dalloc(&b->d_scales, 1));
+    b->tw.log2n = b->log2n;
+    b->tw.shift = (b->log2n + 1) / 2;
+    chk(dalloc(&b->tw.lo64, int64_t(1) << b->tw.shift));
+    chk(dalloc(&b->tw.hi64, int64_t(1) << (b->log2n - b->tw.shift)));
+    chk(dalloc(&b->tw.lo32, int64_t(1) << b->tw.shift));
+    chk(dalloc(&b->tw.hi32, int64_t(1) << (b->log2n - b->tw.shift)));
     chk(dalloc(&b->d_trig, b->trig_cap));
     chk(dalloc(&b->d_trig_count, 1));
     chk(dalloc(&b->d_err, 1));
+    b->h_c0.resize(nt);
+    for (int64_t t = 0; t < nt; ++t) b->h_c0[t] = coef[t * kNB];
     if (b->fused) {
-        fused_default_tiling(b->log2n, &b->n1, &b->ccols, &b->rpc);
-        b->n2 = (int)(b->n / b->n1);
-        const size_t per = (size_t)b->n * ((d.flags & CUI_STORE_BF16) ? 4 : 8);
-        b->batch = (int)std::max<int64_t>(1, std::min<int64_t>(4096, ((int64_t)1 << 30) / (int64_t)per));
-        b->batch = (int)std::min<int64_t>(b->batch, nt);
-        const int64_t na = (int64_t)(b->n1 / 2) * (b->n2 / b->ccols);
-        chk(dalloc(&b->d_basis, na * kNB));
-        chk(dalloc(&b->d_basis_df, na * kNB));
-        chk(cudaMalloc(&b->d_y, per * (size_t)b->batch));
-        b->h_kex.resize(nt);
-        for (int64_t t = 0; t < nt; ++t) {
-            b->h_kex[t] = exact_bound(coef[t * kNB], b->ccols, b->nh);
-            b->kx = std::max(b->kx, b->h_kex[t]);
-        }
-        chk(dalloc(&b->d_kex, nt));
-        chk(dalloc(&b->d_gexact, (int64_t)std::max(1, b->kx) * kNB));
-        chk(dalloc(&b->d_win, (int64_t)b->batch * std::max(1, b->nwin)));
+        // tiling and its buffers are set up after the constants are on the device
     } else {
         const size_t rs = b->plain_fp64 ? sizeof(double2) : sizeof(float2);
         chk(cudaMalloc(&b->d_dS, rs * b->nh));
@@ -389,12 +441,13 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     chk(cudaMemsetAsync(b->d_err, 0, sizeof(int), s));
     chk(cudaMemsetAsync(b->d_trig_count, 0, sizeof(unsigned long long), s));
     launch_amp_table(b->d_amp, b->nh, s);
+    launch_twiddle_tables(b->tw, s);
     if (b->fused) {
-        chk(cudaMemsetAsync(b->d_win, 0, sizeof(Slot) * (size_t)b->batch * std::max(1, b->nwin), s));
-        launch_basis_table(b->d_basis, b->d_basis_df, b->n1, b->n2, b->ccols, s);
-        chk(cudaMemcpyAsync(b->d_kex, b->h_kex.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
-        launch_exact_table(b->d_gexact, b->kx, s);
-        fused_set_consts(make_deriv_consts(), s);
+        cui_tuning tu;
+        fused_default_tiling(b->log2n, &tu.n1, &tu.ccols, &tu.rpc);
+        const int64_t per = b->n * ((d.flags & CUI_STORE_BF16) ? 4 : 8);
+        tu.batch = (int32_t)std::min<int64_t>(nt, std::max<int64_t>(1, std::min<int64_t>(4096, (1ll << 30) / per)));
+        chk(configure_fused(b, tu));
     } else {
         chk(cudaMemsetAsync(b->d_pwin, 0, sizeof(Slot) * std::max(1, b->nwin), s));
     }
@@ -437,7 +490,7 @@ extern "C" cui_status cui_segment_upload(cui_bank b, const double *strain, int64
     Span span(b, 0);
     launch_real_to_complex(b->d_strain, b->d_fa, b->n, s);
     double2 *X = nullptr;
-    launch_fft_passes_f64(b->d_fa, b->d_fb, b->log2n, -1, s, &X);
+    launch_fft_passes_f64(b->d_fa, b->d_fb, b->log2n, -1, b->tw, s, &X);
     launch_weighted_data(X, b->d_psd, b->d_amp, b->n, b->k_low, b->desc.sample_rate, b->d_scales, b->d_wbar,
                          b->d_dS, b->plain_fp64, s);
     launch_prefix(b->d_psd, b->d_amp, b->n, b->k_low, b->d_prefix, b->d_scan, s);
@@ -478,7 +531,7 @@ static FusedArgs fused_args(cui_bank b, const int32_t *order, int64_t base)
     a.window = b->desc.window;
     a.nwin = b->nwin;
     a.thr2 = (float)(b->desc.snr_threshold * b->desc.snr_threshold);
-    a.df = (b->desc.flags & CUI_PSI_DF) != 0;
+    a.fp64 = (b->desc.flags & CUI_PSI_FP64) != 0;
     a.bf16 = (b->desc.flags & CUI_STORE_BF16) != 0;
     return a;
 }
@@ -547,6 +600,7 @@ extern "C" cui_status cui_filter_bank(cui_bank b, const int32_t *order, int64_t 
         a.psd = b->d_psd;
         a.dS = b->d_dS;
         a.scales = b->d_scales;
+        a.tw = b->tw;
         a.h = b->d_h;
         a.qa = b->d_qa;
         a.qb = b->d_qb;
@@ -576,6 +630,77 @@ extern "C" cui_status cui_filter_bank(cui_bank b, const int32_t *order, int64_t 
         }
     }
     b->have_peaks = peaks_dev == nullptr;
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_bank_get_tuning(cui_bank b, cui_tuning *out)
+{
+    if (!b || !out) return fail(CUI_ERR_ARG, "bank and out must be non-NULL");
+    if (!b->fused) return fail(CUI_ERR_STATE, "the bank runs the per-template path, which has no tiling");
+    *out = cui_tuning{b->n1, b->ccols, b->rpc, b->batch};
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_bank_set_tuning(cui_bank b, const cui_tuning *tu)
+{
+    if (!b || !tu) return fail(CUI_ERR_ARG, "bank and tuning must be non-NULL");
+    if (!b->fused) return fail(CUI_ERR_STATE, "the bank runs the per-template path, which has no tiling");
+    if (tu->n1 <= 0 || b->n % tu->n1 || !fused_tiling_ok(b->log2n, tu->n1, tu->ccols, tu->rpc) || tu->batch < 1)
+        return fail(CUI_ERR_ARG, "no kernels for n1 = %d, ccols = %d, rpc = %d, batch = %d at N = %lld", tu->n1,
+                    tu->ccols, tu->rpc, tu->batch, (long long)b->n);
+    CUI_TRY(configure_fused(b, *tu), "cui_bank_set_tuning");
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_bank_autotune(cui_bank b, int32_t reps, cui_tuning *best, double *best_ms)
+{
+    if (!b || reps < 1) return fail(CUI_ERR_ARG, "bank must be non-NULL and reps >= 1");
+    if (!b->fused) return fail(CUI_ERR_STATE, "the bank runs the per-template path, which has no tiling");
+    if (!b->have_segment) return fail(CUI_ERR_STATE, "autotuning times the uploaded segment: upload one first");
+    const cudaStream_t s = b->stream;
+    const bool trace = b->trace;
+    b->trace = false;
+    cudaEvent_t e0, e1;
+    CUI_TRY(cudaEventCreate(&e0), "autotune events");
+    CUI_TRY(cudaEventCreate(&e1), "autotune events");
+    cui_tuning cur = {b->n1, b->ccols, b->rpc, b->batch}, top = cur;
+    double top_ms = 1e300;
+    const int n1s[] = {64, 128, 256}, ccs[] = {32, 64}, rpcs[] = {1, 2, 4, 8, 16, 32};
+    const int64_t per = b->n * ((b->desc.flags & CUI_STORE_BF16) ? 4 : 8);
+    std::vector<int> batches;
+    for (int64_t bt = 16; bt <= 4096; bt *= 4)
+        if (bt * per <= (4ll << 30)) batches.push_back((int)bt);
+    for (int n1 : n1s)
+        for (int cc : ccs)
+            for (int rp : rpcs) {
+                if (!fused_tiling_ok(b->log2n, n1, cc, rp)) continue;
+                for (int bt : batches) {
+                    cui_tuning tu = {n1, cc, rp, bt};
+                    if (configure_fused(b, tu) != cudaSuccess) {
+                        cudaGetLastError();
+                        continue;
+                    }
+                    cui_status st = cui_filter_bank(b, nullptr, b->nt, nullptr);
+                    if (st != CUI_OK) continue;
+                    cudaEventRecord(e0, s);
+                    for (int r = 0; r < reps; ++r) cui_filter_bank(b, nullptr, b->nt, nullptr);
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms / reps < top_ms) {
+                        top_ms = ms / reps;
+                        top = tu;
+                    }
+                    if (bt >= b->nt) break; // larger batches change nothing
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->trace = trace;
+    CUI_TRY(configure_fused(b, top_ms < 1e300 ? top : cur), "autotune: selecting the best tiling");
+    if (best) *best = cui_tuning{b->n1, b->ccols, b->rpc, b->batch};
+    if (best_ms) *best_ms = top_ms;
     return CUI_OK;
 }
 
@@ -686,24 +811,7 @@ extern "C" cui_status cui_bank_template(cui_bank b, int64_t t, float *out_dev)
         if (!b->d_basis) {
             fused_default_tiling(b->log2n, &b->n1, &b->ccols, &b->rpc);
             b->n2 = (int)(b->n / b->n1);
-            const int64_t na = (int64_t)(b->n1 / 2) * (b->n2 / b->ccols);
-            CUI_TRY(dalloc(&b->d_basis, na * kNB), "basis table");
-            CUI_TRY(dalloc(&b->d_basis_df, na * kNB), "basis table");
-            launch_basis_table(b->d_basis, b->d_basis_df, b->n1, b->n2, b->ccols, b->stream);
-            std::vector<double> c(kNB);
-            b->h_kex.assign(b->nt, 0);
-            for (int64_t i = 0; i < b->nt; ++i) {
-                CUI_TRY(cudaMemcpy(c.data(), b->d_coef + i * kNB, sizeof(double) * kNB, cudaMemcpyDeviceToHost),
-                        "coefficients");
-                b->h_kex[i] = exact_bound(c[0], b->ccols, b->nh);
-                b->kx = std::max(b->kx, b->h_kex[i]);
-            }
-            CUI_TRY(dalloc(&b->d_kex, b->nt), "exact bounds");
-            CUI_TRY(dalloc(&b->d_gexact, (int64_t)std::max(1, b->kx) * kNB), "exact table");
-            CUI_TRY(cudaMemcpy(b->d_kex, b->h_kex.data(), sizeof(int32_t) * b->nt, cudaMemcpyHostToDevice),
-                    "exact bounds");
-            launch_exact_table(b->d_gexact, b->kx, b->stream);
-            fused_set_consts(make_deriv_consts(), b->stream);
+            CUI_TRY(build_phase_tables(b, b->n1, b->ccols), "template read-out tables");
         }
     }
     FusedArgs a = fused_args(b, b->d_iota, 0);

@@ -119,6 +119,103 @@ template <int R, int SIGN, typename C> CUI_HD void dft(C *v)
     else dft16<SIGN>(v);
 }
 
+// --------------------------------------------- input-pruned DFTs --------
+// DFT4 of (a, b, 0, 0): inputs v2, v3 are not read.
+template <int SIGN, typename C> CUI_HD void dft4_lo2(C &v0, C &v1, C &v2, C &v3)
+{
+    const C a = v0, b = v1, sb = mul_si<SIGN>(b);
+    v0 = a + b;
+    v1 = a + sb;
+    v2 = a - b;
+    v3 = a - sb;
+}
+
+// DFT_R of v when only v[0 .. NZ) can be nonzero (NZ a power of two <= R):
+// the butterflies that would only combine known zeros are skipped, and the
+// inputs v[NZ ..) are never read.  Same decompositions as dft8 / dft16.
+template <int NZ, int SIGN, typename C> CUI_HD void dft8_nz(C *v)
+{
+    using R = decltype(v[0].x);
+    if constexpr (NZ >= 8) {
+        dft8<SIGN>(v);
+    } else if constexpr (NZ == 1) {
+#pragma unroll
+        for (int i = 1; i < 8; ++i) v[i] = v[0];
+    } else {
+        // r = r1 + 2 r2: first layer over r2
+        if constexpr (NZ == 4) {
+            dft4_lo2<SIGN>(v[0], v[2], v[4], v[6]);
+            dft4_lo2<SIGN>(v[1], v[3], v[5], v[7]);
+        } else { // NZ == 2: r2 = 0 only
+            v[2] = v[4] = v[6] = v[0];
+            v[3] = v[5] = v[7] = v[1];
+        }
+        v[3] = w8<SIGN, C, R>(v[3], 1);
+        v[5] = w8<SIGN, C, R>(v[5], 2);
+        v[7] = w8<SIGN, C, R>(v[7], 3);
+        C y[8];
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+            y[k2] = v[2 * k2] + v[2 * k2 + 1];
+            y[k2 + 4] = v[2 * k2] - v[2 * k2 + 1];
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = y[i];
+    }
+}
+
+template <int NZ, int SIGN, typename C> CUI_HD void dft16_nz(C *v)
+{
+    using R = decltype(v[0].x);
+    if constexpr (NZ >= 16) {
+        dft16<SIGN>(v);
+    } else if constexpr (NZ == 1) {
+#pragma unroll
+        for (int i = 1; i < 16; ++i) v[i] = v[0];
+    } else {
+        // r = r1 + 4 r2: first layer over r2 gives a[r1][k2] at v[r1 + 4 k2]
+        if constexpr (NZ == 8) {
+#pragma unroll
+            for (int r1 = 0; r1 < 4; ++r1) dft4_lo2<SIGN>(v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12]);
+        } else { // NZ == 2 or 4: r2 = 0 only
+#pragma unroll
+            for (int r1 = 0; r1 < NZ; ++r1) v[r1 + 4] = v[r1 + 8] = v[r1 + 12] = v[r1];
+        }
+        const R c1 = k16<R>::c1, s1 = k16<R>::s1, h = k16<R>::r2;
+        v[5] = cmul(v[5], mk(c1, SIGN * s1));
+        v[9] = cmul(v[9], mk(h, SIGN * h));
+        v[13] = cmul(v[13], mk(s1, SIGN * c1));
+        if constexpr (NZ >= 4) {
+            v[6] = cmul(v[6], mk(h, SIGN * h));
+            v[10] = mul_si<SIGN>(v[10]);
+            v[14] = cmul(v[14], mk(-h, SIGN * h));
+            v[7] = cmul(v[7], mk(s1, SIGN * c1));
+            v[11] = cmul(v[11], mk(-h, SIGN * h));
+            v[15] = cmul(v[15], mk(-c1, -SIGN * s1));
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+            if constexpr (NZ >= 4) dft4<SIGN>(v[4 * k2], v[4 * k2 + 1], v[4 * k2 + 2], v[4 * k2 + 3]);
+            else dft4_lo2<SIGN>(v[4 * k2], v[4 * k2 + 1], v[4 * k2 + 2], v[4 * k2 + 3]);
+        }
+        C y[16];
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2)
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) y[k2 + 4 * k1] = v[4 * k2 + k1];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = y[i];
+    }
+}
+
+template <int R, int NZ, int SIGN, typename C> CUI_HD void dft_nz(C *v)
+{
+    if constexpr (NZ >= R) dft<R, SIGN>(v);
+    else if constexpr (R == 8) dft8_nz<NZ, SIGN>(v);
+    else if constexpr (R == 16) dft16_nz<NZ, SIGN>(v);
+    else dft<R, SIGN>(v); // radix 2 and 4 are not pruned (their inputs are zero-filled by the caller)
+}
+
 // ---------------------------------------------- double-float arithmetic ---
 // Error-free transformations (Knuth's two-sum, FMA two-product; Dekker 1971)
 // on FP32 pairs hi + lo, with intrinsics so no operation is contracted or

@@ -73,11 +73,14 @@ __device__ __forceinline__ float4 anchor_derivs(float phi0, const float *tf, flo
 }
 
 // (Phi(k_a) mod 1, Phi'(k_a) mod 1, Phi''(k_a)/2, Phi'''(k_a)/6) in cycles.
+// Default: the nine products c_i g_i(k_a) in double-float (FMA two-products,
+// two-sum accumulation of the high parts, plain accumulation of the low
+// parts); p.fp64 selects native FP64 instead.
 __device__ __forceinline__ float4 anchor_eval(const FusedArgs &p, int t, int64_t ai, float ka)
 {
     float tf[kNB];
     float phi0, u7, c5;
-    if (!p.df) {
+    if (p.fp64) {
         const double *c = p.coef + (int64_t)t * kNB;
         const double *g = p.basis + ai * kNB;
         double T[kNB];
@@ -95,16 +98,22 @@ __device__ __forceinline__ float4 anchor_eval(const FusedArgs &p, int t, int64_t
     } else {
         const float2 *c = p.coef_df + (int64_t)t * kNB;
         const float2 *g = p.basis_df + ai * kNB;
-        df s = {0.0f, 0.0f};
+        float s = 0.f, e = 0.f;
 #pragma unroll
         for (int i = 0; i < kNB; ++i) {
-            float2 ci = c[i], gi = g[i];
-            df T = df_mul(df{ci.x, ci.y}, df{gi.x, gi.y});
-            s = df_add(s, T);
-            tf[i] = T.hi;
+            const float2 ci = c[i], gi = g[i];
+            const float ph = __fmul_rn(ci.x, gi.x);
+            float pe = __fmaf_rn(ci.x, gi.x, -ph);
+            pe = __fmaf_rn(ci.x, gi.y, pe);
+            pe = __fmaf_rn(ci.y, gi.x, pe);
+            const float sn = __fadd_rn(s, ph);
+            const float bb = __fsub_rn(sn, s);
+            const float er = __fadd_rn(__fsub_rn(s, __fsub_rn(sn, bb)), __fsub_rn(ph, bb));
+            s = sn;
+            e = __fadd_rn(e, __fadd_rn(er, pe));
+            tf[i] = ph;
         }
-        float h = __fsub_rn(s.hi, rintf(s.hi));
-        phi0 = h + s.lo;
+        phi0 = __fadd_rn(__fsub_rn(s, rintf(s)), e);
         u7 = c[7].x * g[6].x;
         c5 = c[5].x;
     }
@@ -141,48 +150,22 @@ __device__ __forceinline__ float2 gen_bin(float4 a, float x, float2 w)
 __device__ __forceinline__ int ceil_div_pos(int num, int den) { return num <= 0 ? 0 : (num + den - 1) / den; }
 
 // ---------------------------------------------------------------- pass 1 ---
-// Grid (n2 / C, B).  C columns, n1 = R0 * R1 rows; thread = (column, j).
-template <int N1, int R0, int R1, int C, typename ST>
-__global__ void __launch_bounds__(C *N1 / 16) k_pass1(const FusedArgs p)
+// Stage 0 of a column block for one template: generate q on rows
+// a = j + r N1/R0 (only r < NZ can fall inside the band, because the band
+// ends below N/2, i.e. below row N1/2) and take the input-pruned R0-point DFT.
+template <int N1, int R0, int C, int NZ>
+__device__ __forceinline__ void p1_stage0(float2 *v, const FusedArgs &p, const float4 *anc, const float2 *cdf, int jt,
+                                          int col, int b0, int a_lo, int a_hi, int klo, int khi, int kex)
 {
-    constexpr int NT = C * N1 / 16;
-    constexpr int NROW = N1 / 2;
-    __shared__ float4 anc[NROW];
-    __shared__ float2 tw[N1];
-    __shared__ float2 cdf[kNB];
-    extern __shared__ float2 sm[]; // [N1][C]
-    const int tid = threadIdx.x;
-    const int col = tid % C;
-    const int jt = tid / C;
-    const int y = blockIdx.y;
-    const int t = p.order[p.base + y];
-    const int cb = blockIdx.x;
-    const int n2 = p.n2;
-    const int b0 = cb * C;
-    const int khi = p.khi[t];
-    const int klo = p.k_low;
-    const int kex = p.kex[t];
-    const int a_lo = ceil_div_pos(klo - b0 - (C - 1), n2);
-    const int a_hi = min(NROW, ceil_div_pos(khi - b0, n2));
-
-    for (int m = tid; m < N1; m += NT) tw[m] = turn(m, N1);
-    if (tid < kNB) cdf[tid] = p.coef_df[(int64_t)t * kNB + tid];
-    for (int a = a_lo + tid; a < a_hi; a += NT) {
-        const int64_t ai = (int64_t)a * (n2 / C) + cb;
-        anc[a] = anchor_eval(p, t, ai, (float)((int64_t)n2 * a + b0 + C / 2));
-    }
-    __syncthreads();
-
-    // stage 0: generate q for rows a = j + r N1/R0 of column b0 + col, DFT over r
     constexpr int T0 = 16 / R0;
-    float2 v[16];
     const float x = (float)(col - C / 2);
     const int bcol = b0 + col;
+    const int n2 = p.n2;
 #pragma unroll
     for (int i = 0; i < T0; ++i) {
         const int j = jt + i * (N1 / 16);
 #pragma unroll
-        for (int r = 0; r < R0; ++r) {
+        for (int r = 0; r < NZ; ++r) {
             const int a = j + r * (N1 / R0);
             float2 q = make_float2(0.f, 0.f);
             if (a >= a_lo && a < a_hi) {
@@ -193,50 +176,156 @@ __global__ void __launch_bounds__(C *N1 / 16) k_pass1(const FusedArgs p)
             }
             v[i * R0 + r] = q;
         }
-        dft<R0, +1>(v + i * R0);
+        dft_nz<R0, NZ, +1>(v + i * R0);
     }
-#pragma unroll
-    for (int i = 0; i < T0; ++i) {
-        const int j = jt + i * (N1 / 16);
-#pragma unroll
-        for (int r = 0; r < R0; ++r) sm[(j * R0 + r) * C + col] = v[i * R0 + r];
-    }
-    __syncthreads();
+}
 
-    // stage 1 (last): radix R1 with sub-transforms of size R0 done
+// Grid (n2 / C, ceil(B / G)).  A CTA owns C columns of n1 = R0 * R1 rows and
+// runs G templates through them, so the twiddles that depend only on the
+// position (the stage-1 table and the inter-pass factors exp(2 pi i b c / N),
+// kept in registers) are computed once per CTA.
+template <int N1, int R0, int R1, int C, int G, typename ST>
+__global__ void __launch_bounds__(C *N1 / 16, (C * N1 / 16 <= 512 ? 2 : 1)) k_pass1(const FusedArgs p, int count)
+{
+    constexpr int NT = C * N1 / 16;
+    constexpr int NROW = N1 / 2;
     constexpr int T1 = 16 / R1;
+    __shared__ float4 anc[NROW];
+    __shared__ float2 tw[N1];
+    __shared__ float2 cdf[kNB];
+    extern __shared__ float2 sm[]; // [N1][C]
+    const int tid = threadIdx.x;
+    const int col = tid % C;
+    const int jt = tid / C;
+    const int cb = blockIdx.x;
+    const int n2 = p.n2;
+    const int b0 = cb * C;
+    const int bcol = b0 + col;
+    const int klo = p.k_low;
     const int64_t N = p.n;
-    ST *yout = (ST *)p.ywork + (size_t)y * (size_t)N;
+
+    for (int m = tid; m < N1; m += NT) tw[m] = turn(m, N1);
+    // exp(2 pi i b c / N) for this thread's stage-1 outputs c = j + r N1/R1 is
+    // ipb[i] * ips^r: one accurate root per task and one step, per CTA
+    float2 ipb[T1];
 #pragma unroll
-    for (int i = 0; i < T1; ++i) {
-        const int j = jt + i * (N1 / 16);
-        float2 *u = v + i * R1;
+    for (int i = 0; i < T1; ++i)
+        ipb[i] = turn(((unsigned)bcol * (unsigned)(jt + i * (N1 / 16))) & (unsigned)(N - 1), (unsigned)N);
+    const float2 ips = turn(((unsigned)bcol * (unsigned)(N1 / R1)) & (unsigned)(N - 1), (unsigned)N);
+
+    for (int g = 0; g < G; ++g) {
+        const int y = blockIdx.y * G + g;
+        if (y >= count) break;
+        const int t = p.order[p.base + y];
+        const int khi = p.khi[t];
+        const int kex = p.kex[t];
+        const int a_lo = ceil_div_pos(klo - b0 - (C - 1), n2);
+        const int a_hi = min(NROW, ceil_div_pos(khi - b0, n2));
+        if (tid < kNB) cdf[tid] = p.coef_df[(int64_t)t * kNB + tid];
+        for (int a = a_lo + tid; a < a_hi; a += NT) {
+            const int64_t ai = (int64_t)a * (n2 / C) + cb;
+            anc[a] = anchor_eval(p, t, ai, (float)((int64_t)n2 * a + b0 + C / 2));
+        }
+        __syncthreads();
+
+        float2 v[16];
+        // number of stage-0 inputs per task that can be nonzero, rounded up to a power of two
+        const int nzr = ceil_div_pos(a_hi, N1 / R0);
+        if (nzr <= 1) p1_stage0<N1, R0, C, 1>(v, p, anc, cdf, jt, col, b0, a_lo, a_hi, klo, khi, kex);
+        else if (nzr <= 2) p1_stage0<N1, R0, C, 2>(v, p, anc, cdf, jt, col, b0, a_lo, a_hi, klo, khi, kex);
+        else if (nzr <= 4 || R0 <= 8) p1_stage0<N1, R0, C, (R0 > 8 ? 4 : R0 / 2)>(v, p, anc, cdf, jt, col, b0, a_lo,
+                                                                                    a_hi, klo, khi, kex);
+        else p1_stage0<N1, R0, C, R0 / 2>(v, p, anc, cdf, jt, col, b0, a_lo, a_hi, klo, khi, kex);
 #pragma unroll
-        for (int r = 0; r < R1; ++r) u[r] = sm[(j + r * (N1 / R1)) * C + col];
-        const int jm = j % R0;
+        for (int i = 0; i < 16 / R0; ++i) {
+            const int j = jt + i * (N1 / 16);
 #pragma unroll
-        for (int r = 1; r < R1; ++r) u[r] = cmul(u[r], tw[jm * r]);
-        dft<R1, +1>(u);
-        // outputs c = j + r N1/R1, times exp(2 pi i b c / N)
-        const unsigned mask = (unsigned)(N - 1);
-        float2 w = turn(((unsigned)bcol * (unsigned)j) & mask, (unsigned)N);
-        const float2 step = turn(((unsigned)bcol * (unsigned)(N1 / R1)) & mask, (unsigned)N);
+            for (int r = 0; r < R0; ++r) sm[(j * R0 + r) * C + col] = v[i * R0 + r];
+        }
+        __syncthreads();
+
+        // stage 1 (last): radix R1 over sub-transforms of size R0; times exp(2 pi i b c / N)
+        ST *yout = (ST *)p.ywork + (size_t)y * (size_t)N;
 #pragma unroll
-        for (int r = 0; r < R1; ++r) {
-            const int c = j + r * (N1 / R1);
-            st_c<ST>(yout + (size_t)c * n2 + bcol, cmul(u[r], w));
-            w = cmul(w, step);
+        for (int i = 0; i < T1; ++i) {
+            const int j = jt + i * (N1 / 16);
+            float2 *u = v + i * R1;
+#pragma unroll
+            for (int r = 0; r < R1; ++r) u[r] = sm[(j + r * (N1 / R1)) * C + col];
+            const int jm = j % R0;
+#pragma unroll
+            for (int r = 1; r < R1; ++r) u[r] = cmul(u[r], tw[jm * r]);
+            dft<R1, +1>(u);
+            float2 w = ipb[i];
+#pragma unroll
+            for (int r = 0; r < R1; ++r) {
+                const int c = j + r * (N1 / R1);
+                st_c<ST>(yout + (size_t)c * n2 + bcol, cmul(u[r], w));
+                w = cmul(w, ips);
+            }
         }
     }
 }
 
 // ---------------------------------------------------------------- pass 2 ---
+// One spare complex slot every 16 keeps the stride-16 stores conflict-free.
 __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
 
-template <int L, int R> __device__ __forceinline__ void p2_twiddle(float2 *u, int j, int Ns)
+// load v[i R + r] = row[j + r L/R] for this thread's tasks j = lt + i L/16
+template <int L, int R> __device__ __forceinline__ void p2_load(float2 *v, const float2 *row, int lt)
 {
-    const int jm = j & (Ns - 1);
-    float2 w = turn((unsigned)jm, (unsigned)(Ns * R));
+    constexpr int TPR = L / 16, T = 16 / R, Q = L / R;
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+        const int j = lt + i * TPR;
+        if constexpr (Q % 16 == 0) {
+            const float2 *b = row + padi(j);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[i * R + r] = b[r * (Q + Q / 16)];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[i * R + r] = row[padi(j + r * Q)];
+        }
+    }
+}
+
+// Stockham output positions (j / NS) NS R + j mod NS + r NS
+template <int L, int R, int NS> __device__ __forceinline__ void p2_store(const float2 *v, float2 *row, int lt)
+{
+    constexpr int TPR = L / 16, T = 16 / R;
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+        const int j = lt + i * TPR;
+        const int idx = (j / NS) * NS * R + (j & (NS - 1));
+        if constexpr (NS % 16 == 0) {
+            float2 *b = row + padi(idx);
+#pragma unroll
+            for (int r = 0; r < R; ++r) b[r * (NS + NS / 16)] = v[i * R + r];
+        } else if constexpr (NS == 1) {
+            float2 *b = row + padi(idx); // idx = R j and (R j mod 16) + r < 16
+#pragma unroll
+            for (int r = 0; r < R; ++r) b[r] = v[i * R + r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) row[padi(idx + r * NS)] = v[i * R + r];
+        }
+    }
+}
+
+// twiddles exp(2 pi i (j mod NS) r / (NS R)) from a table laid out r-major,
+// tw[r NS + jm], so that consecutive lanes read consecutive words
+template <int R> __device__ __forceinline__ void p2_tw_table(float2 *u, int j, int NS, const float2 *tw)
+{
+    const float2 *t = tw + (j & (NS - 1));
+#pragma unroll
+    for (int r = 1; r < R; ++r) u[r] = cmul(u[r], t[r * NS]);
+}
+
+// the same by powers of one accurately computed root
+template <int R> __device__ __forceinline__ void p2_tw_pow(float2 *u, int j, int NS)
+{
+    const int jm = j & (NS - 1);
+    const float2 w = turn((unsigned)jm, (unsigned)(NS * R));
     float2 wr = w;
 #pragma unroll
     for (int r = 1; r < R; ++r) {
@@ -245,29 +334,39 @@ template <int L, int R> __device__ __forceinline__ void p2_twiddle(float2 *u, in
     }
 }
 
-// middle stage: smem -> registers -> smem (in place, synchronised)
-template <int L, int R, int NS> __device__ __forceinline__ void p2_mid(float2 *v, float2 *row, int lt)
+template <int L, int R, int NS, bool TABLE>
+__device__ __forceinline__ void p2_stage(float2 *v, float2 *row, int lt, const float2 *tw)
 {
-    constexpr int TPR = L / 16;
-    constexpr int T = 16 / R;
+    constexpr int TPR = L / 16, T = 16 / R;
+    p2_load<L, R>(v, row, lt);
 #pragma unroll
     for (int i = 0; i < T; ++i) {
         const int j = lt + i * TPR;
-        float2 *u = v + i * R;
-#pragma unroll
-        for (int r = 0; r < R; ++r) u[r] = row[padi(j + r * (L / R))];
-        if (NS > 1) p2_twiddle<L, R>(u, j, NS);
-        dft<R, +1>(u);
+        if constexpr (TABLE) p2_tw_table<R>(v + i * R, j, NS, tw);
+        else p2_tw_pow<R>(v + i * R, j, NS);
+        dft<R, +1>(v + i * R);
     }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < T; ++i) {
-        const int j = lt + i * TPR;
-        const int idx = (j / NS) * NS * R + (j & (NS - 1));
-#pragma unroll
-        for (int r = 0; r < R; ++r) row[padi(idx + r * NS)] = v[i * R + r];
-    }
-    __syncthreads();
+}
+
+// Rare path of the epilogue (some sample of this thread is above threshold):
+// raise the window maxima.  Kept out of line so that the common path does not
+// carry its registers.
+template <int L, int RL>
+__device__ __noinline__ void p2_triggers(const float2 *v, const FusedArgs &p, int y, int c, int lt, int dlo, int dhi,
+                                         float inv)
+{
+    constexpr int TPR = L / 16, TL = 16 / RL;
+    for (int r = 0; r < RL; ++r)
+        for (int i = 0; i < TL; ++i) {
+            const int d = lt + i * TPR + r * (L / RL);
+            const float2 z = v[i * RL + r];
+            const float r2 = fmaf(z.x, z.x, z.y * z.y) * inv;
+            if (r2 > p.thr2 && d >= dlo && d < dhi) {
+                const int64_t s = (int64_t)c + (int64_t)p.n1 * d;
+                slot_max(p.win + (size_t)y * p.nwin + (int)((s - p.lo) / p.window), make_key(r2, (uint32_t)s),
+                         atan2f(z.y, z.x), p.err);
+            }
+        }
 }
 
 // Grid (n1 / RPC, B).  RPC rows of length L, L/16 threads per row.
@@ -277,8 +376,12 @@ __global__ void __launch_bounds__(RPC *L / 16) k_pass2(const FusedArgs p)
     constexpr int TPR = L / 16;
     constexpr int NT = RPC * TPR;
     constexpr int LP = L + L / 16;
-    constexpr int NW = (NT + 31) / 32;
+    constexpr int NW = NT / 32;
+    constexpr int RL = R3 > 1 ? R3 : (R2 > 1 ? R2 : R1);
+    constexpr int NSL = L / RL;
+    constexpr int TL = 16 / RL;
     extern __shared__ float2 sm[];
+    __shared__ float2 tw1[R0 * R1]; // stage-1 twiddles (sub-transform size R0)
     __shared__ unsigned long long s_key[NW];
     __shared__ float s_zr[NW], s_zi[NW];
     const int tid = threadIdx.x;
@@ -288,9 +391,10 @@ __global__ void __launch_bounds__(RPC *L / 16) k_pass2(const FusedArgs p)
     const int c = blockIdx.x * RPC + rr;
     float2 *row = sm + rr * LP;
     const ST *src = (const ST *)p.ywork + (size_t)y * (size_t)p.n + (size_t)c * L;
+    // tw1[r R0 + jm] = exp(2 pi i jm r / (R0 R1))
+    for (int m = tid; m < R0 * R1; m += NT) tw1[m] = turn((m % R0) * (m / R0), R0 * R1);
 
     float2 v[16];
-    // stage 0 straight from global memory (no twiddle)
     {
         constexpr int T = 16 / R0;
 #pragma unroll
@@ -300,72 +404,66 @@ __global__ void __launch_bounds__(RPC *L / 16) k_pass2(const FusedArgs p)
             for (int r = 0; r < R0; ++r) v[i * R0 + r] = ld_c<ST>(src + j + r * (L / R0));
             dft<R0, +1>(v + i * R0);
         }
-#pragma unroll
-        for (int i = 0; i < T; ++i) {
-            const int j = lt + i * TPR;
-#pragma unroll
-            for (int r = 0; r < R0; ++r) row[padi(j * R0 + r)] = v[i * R0 + r];
-        }
+        p2_store<L, R0, 1>(v, row, lt);
         __syncthreads();
     }
-    // middle stages, then the last stage's radix and sub-transform size
-    constexpr int RL = R3 > 1 ? R3 : (R2 > 1 ? R2 : R1);
-    constexpr int NSL = L / RL;
-    if constexpr (R2 > 1) p2_mid<L, R1, R0>(v, row, lt);
-    if constexpr (R3 > 1) p2_mid<L, R2, R0 * R1>(v, row, lt);
-    // last stage into registers
-    constexpr int TL = 16 / RL;
-#pragma unroll
-    for (int i = 0; i < TL; ++i) {
-        const int j = lt + i * TPR;
-        float2 *u = v + i * RL;
-#pragma unroll
-        for (int r = 0; r < RL; ++r) u[r] = row[padi(j + r * (L / RL))];
-        p2_twiddle<L, RL>(u, j, NSL);
-        dft<RL, +1>(u);
-    }
-
-    // epilogue: rho^2 at samples s = c + n1 (j + r L/RL)
-    const float inv = p.invnorm[t];
-    const int64_t lo = p.lo, hi = p.hi;
-    unsigned long long best = 0ull;
-    float bzr = 0.f, bzi = 0.f;
-#pragma unroll
-    for (int i = 0; i < TL; ++i) {
-        const int j = lt + i * TPR;
-#pragma unroll
-        for (int r = 0; r < RL; ++r) {
-            const float2 z = v[i * RL + r];
-            const int64_t s = (int64_t)c + (int64_t)p.n1 * (j + r * (L / RL));
-            if (s >= lo && s < hi) {
-                const float r2 = (z.x * z.x + z.y * z.y) * inv;
-                const unsigned long long key = make_key(r2, (uint32_t)s);
-                if (key > best) {
-                    best = key;
-                    bzr = z.x;
-                    bzi = z.y;
-                }
-                if (r2 > p.thr2) {
-                    const int m = (int)((s - lo) / p.window);
-                    slot_max(p.win + (size_t)y * p.nwin + m, key, atan2f(z.y, z.x), p.err);
-                }
-            }
+    if constexpr (R2 > 1) {
+        p2_stage<L, R1, R0, true>(v, row, lt, tw1);
+        __syncthreads();
+        p2_store<L, R1, R0>(v, row, lt);
+        __syncthreads();
+        if constexpr (R3 > 1) {
+            p2_stage<L, R2, R0 * R1, false>(v, row, lt, tw1);
+            __syncthreads();
+            p2_store<L, R2, R0 * R1>(v, row, lt);
+            __syncthreads();
         }
     }
-    warp_max_key(best, bzr, bzi);
+    p2_stage<L, RL, NSL, R2 == 1>(v, row, lt, tw1);
+
+    // Epilogue.  Output d = j + r L/RL of this row is sample s = c + n1 d; in
+    // (r, i) order d increases, so the strict '>' keeps the lowest sample
+    // among equal |z|^2.  |z|^2 is compared before the (positive) scaling.
+    const float inv = p.invnorm[t];
+    const int n1 = p.n1;
+    const int64_t lo = p.lo, hi = p.hi;
+    int dlo = 0, dhi = L;
+    if (!(lo <= c && (int64_t)c + (int64_t)n1 * (L - 1) < hi)) {
+        dlo = (int)max((int64_t)0, (lo - c + n1 - 1) / n1);
+        dhi = (int)min((int64_t)L, hi > c ? (hi - c + n1 - 1) / n1 : (int64_t)0);
+    }
+    float best = -1.f, bzr = 0.f, bzi = 0.f;
+    int bd = 0;
+#pragma unroll
+    for (int r = 0; r < RL; ++r)
+#pragma unroll
+        for (int i = 0; i < TL; ++i) {
+            const int d = lt + i * TPR + r * (L / RL);
+            const float2 z = v[i * RL + r];
+            const float m = fmaf(z.x, z.x, z.y * z.y);
+            if (m > best && d >= dlo && d < dhi) {
+                best = m;
+                bd = d;
+                bzr = z.x;
+                bzi = z.y;
+            }
+        }
+    if (best * inv > p.thr2) p2_triggers<L, RL>(v, p, y, c, lt, dlo, dhi, inv);
+    unsigned long long key = best >= 0.f ? make_key(best * inv, (uint32_t)(c + n1 * bd)) : 0ull;
+    warp_max_key(key, bzr, bzi);
     const int lane = tid & 31, wid = tid >> 5;
     if (lane == 0) {
-        s_key[wid] = best;
+        s_key[wid] = key;
         s_zr[wid] = bzr;
         s_zi[wid] = bzi;
     }
     __syncthreads();
     if (wid == 0) {
-        best = lane < NW ? s_key[lane] : 0ull;
+        key = lane < NW ? s_key[lane] : 0ull;
         bzr = lane < NW ? s_zr[lane] : 0.f;
         bzi = lane < NW ? s_zi[lane] : 0.f;
-        warp_max_key(best, bzr, bzi);
-        if (lane == 0 && best != 0ull) slot_max(p.peak + t, best, atan2f(bzi, bzr), p.err);
+        warp_max_key(key, bzr, bzi);
+        if (lane == 0 && key != 0ull) slot_max(p.peak + t, key, atan2f(bzi, bzr), p.err);
     }
 }
 
@@ -376,10 +474,25 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+constexpr int kPass1Group = 4; // templates per pass-1 CTA
+
 size_t fused_pass1_smem(int n1, int ccols) { return (size_t)n1 * ccols * sizeof(float2); }
 size_t fused_pass2_smem(int n2, int rpc) { return (size_t)rpc * (n2 + n2 / 16) * sizeof(float2); }
 
 bool fused_supported(int log2n) { return log2n >= 12 && log2n <= 22; }
+
+// A tiling has kernels when pass 1 exists for (n1, ccols) and pass 2 for (n2, rpc).
+bool fused_tiling_ok(int log2n, int n1, int ccols, int rpc)
+{
+    if (!fused_supported(log2n) || (n1 != 64 && n1 != 128 && n1 != 256) || (ccols != 32 && ccols != 64)) return false;
+    const int64_t n2 = (int64_t(1) << log2n) / n1;
+    if (n2 % ccols) return false;
+    static const int pass2[][2] = {{64, 32},  {128, 16}, {256, 8},  {512, 4},  {1024, 4},
+                                   {2048, 2}, {4096, 2}, {4096, 1}, {8192, 1}, {16384, 1}};
+    for (auto &q : pass2)
+        if (q[0] == n2 && q[1] == rpc) return true;
+    return false;
+}
 
 void fused_default_tiling(int log2n, int *n1, int *ccols, int *rpc)
 {
@@ -394,12 +507,12 @@ void fused_default_tiling(int log2n, int *n1, int *ccols, int *rpc)
 template <int N1, int R0, int R1, int C, typename ST>
 static cudaError_t run_pass1(const FusedArgs &a, int count, cudaStream_t s)
 {
-    auto k = k_pass1<N1, R0, R1, C, ST>;
+    auto k = k_pass1<N1, R0, R1, C, kPass1Group, ST>;
     const size_t smem = fused_pass1_smem(N1, C);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)(a.n2 / C), (unsigned)count);
-    k<<<grid, C * N1 / 16, smem, s>>>(a);
+    dim3 grid((unsigned)(a.n2 / C), (unsigned)((count + kPass1Group - 1) / kPass1Group));
+    k<<<grid, C * N1 / 16, smem, s>>>(a, count);
     return cudaGetLastError();
 }
 

@@ -34,8 +34,18 @@ struct DerivConsts {
 };
 
 // ------------------------------------------------------------- segment.cu --
-void launch_fft_passes_f64(double2 *a, double2 *b, int log2n, int sign, cudaStream_t s, double2 **result);
-void launch_fft_passes_f32(float2 *a, float2 *b, int log2n, int sign, cudaStream_t s, float2 **result);
+// Two-level twiddle tables of a length-2^log2n transform:
+// exp(2 pi i m / 2^log2n) = hi[m >> shift] * lo[m & (2^shift - 1)].
+struct Twiddles {
+    double2 *lo64, *hi64;
+    float2 *lo32, *hi32;
+    int shift, log2n;
+};
+void launch_twiddle_tables(const Twiddles &t, cudaStream_t s);
+void launch_fft_passes_f64(double2 *a, double2 *b, int log2n, int sign, const Twiddles &tw, cudaStream_t s,
+                           double2 **result);
+void launch_fft_passes_f32(float2 *a, float2 *b, int log2n, int sign, const Twiddles &tw, cudaStream_t s,
+                           float2 **result);
 void launch_real_to_complex(const double *d, double2 *out, int64_t n, cudaStream_t s);
 void launch_amp_table(double *amp, int64_t nhalf, cudaStream_t s);
 void launch_weighted_data(const double2 *X, const double *psd, const double *amp, int64_t n, int k_low,
@@ -70,11 +80,12 @@ struct FusedArgs {
     int64_t lo, hi, window;
     int nwin;
     float thr2;
-    bool df;
+    bool fp64; // anchor phases in FP64 instead of double-float
     bool bf16;
 };
 void fused_set_consts(const DerivConsts &dc, cudaStream_t s);
 bool fused_supported(int log2n);
+bool fused_tiling_ok(int log2n, int n1, int ccols, int rpc);
 void fused_default_tiling(int log2n, int *n1, int *ccols, int *rpc);
 size_t fused_pass1_smem(int n1, int ccols);
 size_t fused_pass2_smem(int n2, int rpc);
@@ -106,6 +117,7 @@ struct PlainArgs {
     const double *psd;       // [N/2+1]
     const void *dS;          // [N/2] scaled d~/S (float2 or double2)
     const SegScales *scales;
+    Twiddles tw;             // FFT twiddle tables
     void *h, *qa, *qb;       // work buffers, N complex each (h: N/2)
     double *acc;             // sigma sum, one double
     Slot *peak, *win;

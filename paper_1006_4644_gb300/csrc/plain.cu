@@ -150,8 +150,8 @@ template <typename Rl> static cudaError_t plain_template(const PlainArgs &a, int
     k_plain_sigma<Rl><<<608, 256, 0, s>>>(a, t, h);
     k_plain_mul<Rl><<<1216, 256, 0, s>>>(a, t, h, qa);
     C *z = nullptr;
-    if constexpr (sizeof(Rl) == 8) launch_fft_passes_f64(qa, qb, a.log2n, +1, s, &z);
-    else launch_fft_passes_f32(qa, qb, a.log2n, +1, s, &z);
+    if constexpr (sizeof(Rl) == 8) launch_fft_passes_f64(qa, qb, a.log2n, +1, a.tw, s, &z);
+    else launch_fft_passes_f32(qa, qb, a.log2n, +1, a.tw, s, &z);
     k_plain_detect<Rl><<<608, 256, 0, s>>>(a, t, z);
     launched(4);
     return cudaGetLastError();

@@ -10,18 +10,19 @@
 namespace cui {
 
 // ------------------------------------------------ Stockham global passes ---
-template <typename Rl> __device__ __forceinline__ cpx_t<Rl> unit_turn(int64_t m, int64_t d, int sign);
-template <> __device__ __forceinline__ double2 unit_turn<double>(int64_t m, int64_t d, int sign)
+// exp(SIGN 2 pi i m / 2^log2n) = hi[m >> shift] * lo[m & (2^shift - 1)]: two
+// small tables, built once per bank (k_twiddle_tables), replace a
+// transcendental call per twiddle.
+template <typename Rl> struct TwTab {
+    const cpx_t<Rl> *lo, *hi;
+    int shift, log2n;
+};
+
+template <typename Rl, int SIGN> __device__ __forceinline__ cpx_t<Rl> tab_turn(const TwTab<Rl> &t, int64_t m)
 {
-    double s, c;
-    sincospi(2.0 * (double)m / (double)d, &s, &c);
-    return make_double2(c, sign * s);
-}
-template <> __device__ __forceinline__ float2 unit_turn<float>(int64_t m, int64_t d, int sign)
-{
-    float s, c;
-    sincospif(2.0f * (float)m / (float)d, &s, &c);
-    return make_float2(c, sign * s);
+    const cpx_t<Rl> a = t.hi[m >> t.shift], b = t.lo[m & ((int64_t(1) << t.shift) - 1)];
+    const cpx_t<Rl> w = cmul(a, b);
+    return SIGN > 0 ? w : mk(w.x, -w.y);
 }
 
 // One radix-R Stockham stage over a length-L transform whose sub-transforms
@@ -30,7 +31,7 @@ template <> __device__ __forceinline__ float2 unit_turn<float>(int64_t m, int64_
 // out[(j / Ns) Ns R + j mod Ns + r Ns].
 template <typename Rl, int R, int SIGN>
 __global__ void __launch_bounds__(256) k_stockham(const cpx_t<Rl> *__restrict__ in, cpx_t<Rl> *__restrict__ out,
-                                                  int64_t L, int64_t Ns)
+                                                  int64_t L, int64_t Ns, int lshift, const TwTab<Rl> tw)
 {
     using C = cpx_t<Rl>;
     const int64_t q = L / R;
@@ -41,8 +42,9 @@ __global__ void __launch_bounds__(256) k_stockham(const cpx_t<Rl> *__restrict__ 
     for (int r = 0; r < R; ++r) v[r] = in[j + r * q];
     const int64_t jm = j & (Ns - 1);
     if (Ns > 1) {
+        // (jm r) / (Ns R) in units of the table's 2^log2n
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], unit_turn<Rl>(jm * r, Ns * R, SIGN));
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tab_turn<Rl, SIGN>(tw, (jm * r) << lshift));
     }
     dft<R, SIGN>(v);
     const int64_t idx = (j / Ns) * Ns * R + jm;
@@ -50,16 +52,20 @@ __global__ void __launch_bounds__(256) k_stockham(const cpx_t<Rl> *__restrict__ 
     for (int r = 0; r < R; ++r) out[idx + r * Ns] = v[r];
 }
 
-template <typename Rl, int SIGN> static void stage(const cpx_t<Rl> *in, cpx_t<Rl> *out, int64_t L, int64_t Ns, int R,
-                                                  cudaStream_t s)
+template <typename Rl, int SIGN>
+static void stage(const cpx_t<Rl> *in, cpx_t<Rl> *out, int64_t L, int64_t Ns, int R, const TwTab<Rl> &tw,
+                  cudaStream_t s)
 {
     const int64_t q = L / R;
     const unsigned blocks = (unsigned)((q + 255) / 256);
+    int lg = 0;
+    while ((int64_t(1) << lg) < Ns * R) ++lg;
+    const int lshift = tw.log2n - lg;
     switch (R) {
-    case 2: k_stockham<Rl, 2, SIGN><<<blocks, 256, 0, s>>>(in, out, L, Ns); break;
-    case 4: k_stockham<Rl, 4, SIGN><<<blocks, 256, 0, s>>>(in, out, L, Ns); break;
-    case 8: k_stockham<Rl, 8, SIGN><<<blocks, 256, 0, s>>>(in, out, L, Ns); break;
-    default: k_stockham<Rl, 16, SIGN><<<blocks, 256, 0, s>>>(in, out, L, Ns); break;
+    case 2: k_stockham<Rl, 2, SIGN><<<blocks, 256, 0, s>>>(in, out, L, Ns, lshift, tw); break;
+    case 4: k_stockham<Rl, 4, SIGN><<<blocks, 256, 0, s>>>(in, out, L, Ns, lshift, tw); break;
+    case 8: k_stockham<Rl, 8, SIGN><<<blocks, 256, 0, s>>>(in, out, L, Ns, lshift, tw); break;
+    default: k_stockham<Rl, 16, SIGN><<<blocks, 256, 0, s>>>(in, out, L, Ns, lshift, tw); break;
     }
     launched();
 }
@@ -67,7 +73,8 @@ template <typename Rl, int SIGN> static void stage(const cpx_t<Rl> *in, cpx_t<Rl
 // Full transform of length 2^log2n: one small-radix stage (if log2n is not a
 // multiple of 4) then radix-16 stages, ping-ponging between a and b.
 template <typename Rl>
-static void fft_passes(cpx_t<Rl> *a, cpx_t<Rl> *b, int log2n, int sign, cudaStream_t s, cpx_t<Rl> **result)
+static void fft_passes(cpx_t<Rl> *a, cpx_t<Rl> *b, int log2n, int sign, const TwTab<Rl> &tw, cudaStream_t s,
+                       cpx_t<Rl> **result)
 {
     const int64_t L = int64_t(1) << log2n;
     int64_t Ns = 1;
@@ -78,8 +85,8 @@ static void fft_passes(cpx_t<Rl> *a, cpx_t<Rl> *b, int log2n, int sign, cudaStre
         int lr = rem ? rem : 4;
         rem = 0;
         int R = 1 << lr;
-        if (sign > 0) stage<Rl, +1>(src, dst, L, Ns, R, s);
-        else stage<Rl, -1>(src, dst, L, Ns, R, s);
+        if (sign > 0) stage<Rl, +1>(src, dst, L, Ns, R, tw, s);
+        else stage<Rl, -1>(src, dst, L, Ns, R, tw, s);
         Ns *= R;
         left -= lr;
         cpx_t<Rl> *t = src;
@@ -89,13 +96,37 @@ static void fft_passes(cpx_t<Rl> *a, cpx_t<Rl> *b, int log2n, int sign, cudaStre
     *result = src;
 }
 
-void launch_fft_passes_f64(double2 *a, double2 *b, int log2n, int sign, cudaStream_t s, double2 **result)
+void launch_fft_passes_f64(double2 *a, double2 *b, int log2n, int sign, const Twiddles &tw, cudaStream_t s,
+                           double2 **result)
 {
-    fft_passes<double>(a, b, log2n, sign, s, result);
+    fft_passes<double>(a, b, log2n, sign, TwTab<double>{tw.lo64, tw.hi64, tw.shift, tw.log2n}, s, result);
 }
-void launch_fft_passes_f32(float2 *a, float2 *b, int log2n, int sign, cudaStream_t s, float2 **result)
+void launch_fft_passes_f32(float2 *a, float2 *b, int log2n, int sign, const Twiddles &tw, cudaStream_t s,
+                           float2 **result)
 {
-    fft_passes<float>(a, b, log2n, sign, s, result);
+    fft_passes<float>(a, b, log2n, sign, TwTab<float>{tw.lo32, tw.hi32, tw.shift, tw.log2n}, s, result);
+}
+
+// lo[i] = exp(2 pi i i / 2^log2n), hi[i] = exp(2 pi i (i << shift) / 2^log2n), in FP64 and FP32
+__global__ void k_twiddle_tables(Twiddles t)
+{
+    const int nlo = 1 << t.shift, nhi = 1 << (t.log2n - t.shift);
+    const double n = (double)(int64_t(1) << t.log2n);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nlo + nhi; i += gridDim.x * blockDim.x) {
+        const int64_t m = i < nlo ? (int64_t)i : ((int64_t)(i - nlo) << t.shift);
+        double s, c;
+        sincospi(2.0 * (double)m / n, &s, &c);
+        double2 *d = i < nlo ? t.lo64 + i : t.hi64 + (i - nlo);
+        float2 *f = i < nlo ? t.lo32 + i : t.hi32 + (i - nlo);
+        *d = make_double2(c, s);
+        *f = make_float2((float)c, (float)s);
+    }
+}
+
+void launch_twiddle_tables(const Twiddles &t, cudaStream_t s)
+{
+    k_twiddle_tables<<<16, 256, 0, s>>>(t);
+    launched();
 }
 
 // -------------------------------------------------------- segment inputs ---

@@ -46,7 +46,7 @@ def seg16s():
     return make_segment(W1)
 
 
-@pytest.mark.parametrize("flags", [0, 1, 4, 12], ids=["fused_fp64", "fused_df", "plain_fp32", "plain_fp64"])
+@pytest.mark.parametrize("flags", [0, 1, 4, 12], ids=["fused_df", "fused_fp64", "plain_fp32", "plain_fp64"])
 def test_seg16s_bank64_all_paths(seg16s, flags):
     from paper_1006_4644_gb300 import CUI_PLAIN
 
@@ -69,14 +69,14 @@ def test_seg16s_bank64_all_paths(seg16s, flags):
 
 
 @pytest.mark.parametrize("log2n", [12, 13, 14, 15, 17, 18, 19])
-@pytest.mark.parametrize("df_anchor", [False, True])
-def test_tiling_sizes_with_ragged_windows(log2n, df_anchor):
+@pytest.mark.parametrize("fp64_anchor", [False, True])
+def test_tiling_sizes_with_ragged_windows(log2n, fp64_anchor):
     n = 1 << log2n
     w = synth.Workload(f"n{log2n}", n, 4096.0, 30.0 if log2n >= 14 else 60.0, 7, 6, 1.0, 6.0, False, 1, 20.0,
                        20.0, 1.0, 777 + log2n)
     strain, psd, dt, plan = make_segment(w)
     lo, hi, window = n // 8, n - n // 5, 1000 if n > 4000 else 333
-    peaks, trig, _ = _run(w, strain, psd, 1 if df_anchor else 0, thr=5.0, window=window, valid=(lo, hi))
+    peaks, trig, _ = _run(w, strain, psd, 1 if fp64_anchor else 0, thr=5.0, window=window, valid=(lo, hi))
     rep = compare_bank(w, dt, psd, peaks, trig, range(w.n_templates), lo, hi, window, 5.0)
     assert rep.ok(), rep
 

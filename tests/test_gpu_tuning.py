@@ -1,0 +1,74 @@
+"""Every tiling the autotuner can choose gives the oracle's answers (GPU), and
+the autotuner leaves a valid, timed tiling selected."""
+
+import itertools
+
+import numpy as np
+import pytest
+
+import synth
+from parity import compare_bank, make_segment
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1006_4644_gb300 import build
+
+    build.build()
+
+
+def _tilings(bank, n):
+    from paper_1006_4644_gb300 import CuiError
+
+    out = []
+    for n1, cc, rpc in itertools.product([64, 128, 256], [32, 64], [1, 2, 4, 8, 16, 32]):
+        try:
+            bank.set_tuning(n1, cc, rpc, 3)
+            out.append((n1, cc, rpc))
+        except CuiError:
+            pass
+    return out
+
+
+@pytest.mark.parametrize("log2n", [14, 20])
+def test_every_tiling_matches_the_oracle(log2n):
+    from paper_1006_4644_gb300 import Bank
+
+    n = 1 << log2n
+    w = synth.Workload(f"tile{log2n}", n, 4096.0, 30.0, 7, 7, 1.0, 8.0, False, 1, 15.0, 15.0, 1.0, 505 + log2n)
+    strain, psd, dt, _ = make_segment(w)
+    m1, m2 = w.masses()
+    with Bank(m1, m2, n=n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, snr_threshold=5.0) as b:
+        b.upload(strain, psd)
+        tilings = _tilings(b, n)
+        assert len(tilings) >= (2 if log2n == 14 else 4), tilings
+        for n1, cc, rpc in tilings:
+            b.set_tuning(n1, cc, rpc, 3)  # batches of 3 leave a ragged last batch
+            assert b.tuning() == {"n1": n1, "ccols": cc, "rpc": rpc, "batch": 3}
+            b.filter()
+            peaks = b.peaks()
+            trig, _ = b.triggers()
+            rep = compare_bank(w, dt, psd, peaks, trig, range(w.n_templates), 0, n, int(w.fs), 5.0)
+            assert rep.ok(), (n1, cc, rpc, rep)
+
+
+def test_autotune_selects_a_valid_tiling():
+    from paper_1006_4644_gb300 import Bank, CuiError
+
+    w = synth.WORKLOADS["seg16s_bank64_pn2"]
+    strain, psd, _, _ = make_segment(w)
+    m1, m2 = w.masses()
+    with Bank(m1, m2, n=w.n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2) as b:
+        with pytest.raises(CuiError):
+            b.autotune()  # needs a segment
+        b.upload(strain, psd)
+        b.filter()
+        ref = b.peaks()
+        tu, ms = b.autotune(reps=1)
+        assert ms > 0 and b.tuning() == tu
+        b.filter()
+        p = b.peaks()
+    assert np.array_equal(p["sample"], ref["sample"])
+    assert np.max(np.abs(p["snr"] - ref["snr"]) / ref["snr"]) < 1e-5
