@@ -202,6 +202,28 @@ typedef struct {
 cui_status cui_trace_enable(cui_bank bank, int on);
 cui_status cui_trace_read(cui_bank bank, cui_trace_stat *host_out, int64_t capacity, int64_t *n);
 
+/* Allocation-free normalisation: sigma_t^2 = 4 df sum_k |h~_k|^2 / S_k of
+ * `count` templates (m1[t], m2[t], host arrays) for the one-sided PSD psd_dev
+ * (N/2 + 1 FP64 values in device memory, read on [k_lo, N/2)), written to
+ * sigma2_dev[0 .. count) (device, caller-owned), asynchronously on `stream`.
+ * No counterpart in the paper: it serves callers that cannot allocate device
+ * memory when they need the result -- work being captured into a CUDA graph,
+ * pipelines whose device memory belongs to one pool allocator, real-time
+ * loops that cannot wait for an allocation -- for instance to renormalise a
+ * bank after a new PSD estimate.  It allocates nothing: its scratch is one
+ * array of about 8.2 MiB compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (with the device current);
+ * make that first call before any stream capture.  Limits: N a power of two
+ * in [64, 2^20], 1 <= count <= 16384; larger values return CUI_ERR_ARG.  All
+ * calls share the array: calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  Same conventions
+ * and units as cui_bank_create; k_lo = ceil(f_low / df), k_hi as there.
+ * Errors: CUI_ERR_ARG, CUI_ERR_CUDA. */
+cui_status cui_template_sigma_noalloc(const double *psd_dev, int64_t n, double sample_rate, double f_low,
+                                      const double *m1, const double *m2, int64_t count, double *sigma2_dev,
+                                      void *stream);
+
 /* Release every resource of the handle (synchronises its stream first).
  * NULL is allowed. */
 void cui_bank_destroy(cui_bank bank);

@@ -71,6 +71,8 @@ def load():
     lib.cui_bank_get_tuning.argtypes = [vp, C.POINTER(cui_tuning)]
     lib.cui_bank_set_tuning.argtypes = [vp, C.POINTER(cui_tuning)]
     lib.cui_bank_autotune.argtypes = [vp, C.c_int32, C.POINTER(cui_tuning), C.POINTER(C.c_double)]
+    lib.cui_template_sigma_noalloc.argtypes = [vp, C.c_int64, C.c_double, C.c_double, vp, vp, C.c_int64, vp, vp]
+    lib.cui_template_sigma_noalloc.restype = C.c_int
     lib.cui_trace_enable.argtypes = [vp, C.c_int]
     lib.cui_trace_read.argtypes = [vp, C.POINTER(cui_trace_stat), C.c_int64, C.POINTER(C.c_int64)]
     lib.cui_bank_destroy.argtypes = [vp]

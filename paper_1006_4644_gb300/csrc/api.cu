@@ -202,6 +202,7 @@ struct cui_bank_s {
 
 namespace cui {
 std::atomic<long long> g_launches{0};
+void set_last_error(const char *msg) { g_err = msg; }
 }
 
 namespace {

@@ -13,6 +13,9 @@ namespace cui {
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
 
+// Message returned by cui_last_error() on this thread.
+void set_last_error(const char *msg);
+
 // Kernel launches issued by this library (read by the tracing calls).
 extern std::atomic<long long> g_launches;
 inline void launched(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
