@@ -202,6 +202,63 @@ typedef struct {
 cui_status cui_trace_enable(cui_bank bank, int on);
 cui_status cui_trace_read(cui_bank bank, cui_trace_stat *host_out, int64_t capacity, int64_t *n);
 
+/* ------------------------------------------------------------------------
+ * Learned prescreen.  Ranks regions of the bank (groups of templates sorted
+ * by chirp mass) from whitened band powers of a segment, so that likely
+ * regions are filtered first.  The paper motivates it only in passing: at
+ * ~10^6 templates brute force "is not the best solution" (introduction,
+ * footnote).  Features: u_k = d~_k sqrt(4 df / S_k) on [f_low, fs/2) split
+ * into `bands` log-spaced bands; per band X_b(j) = sum_{k in band} u_k
+ * exp(+2 pi i j k / N); F[b][m] = log(mean_{frame m} |X_b|^2 / (2 n_b)) over
+ * N / frame frames.  Network: 4 conv1d layers of 32 channels (kernel 5,
+ * stride 1 then 2, zero padding 2, ReLU), per-channel mean and max over time,
+ * linear 64 -> 128 (ReLU) -> regions; BF16 weights, FP32 accumulation; soft
+ * label cross-entropy; Adam.  Training is deterministic for a given seed.
+ * Device arrays: features [count][bands][N/frame] float, targets and scores
+ * [count][regions] float.  Asynchronous on desc.stream unless stated.
+ * ------------------------------------------------------------------------ */
+typedef struct cui_prescreen_s *cui_prescreen;
+
+typedef struct {
+    int64_t n;          /* segment length of the features: power of two in [2^10, 2^22] */
+    double sample_rate; /* Hz */
+    double f_low;       /* Hz, lower edge of the lowest band */
+    int32_t bands;      /* 1 .. 16 */
+    int32_t frame;      /* samples per frame: a multiple of 32 dividing n, n / frame in [8, 256] */
+    int32_t regions;    /* outputs, 2 .. 256 */
+    int32_t max_batch;  /* largest training / gradient batch, 1 .. 4096 */
+    float lr, beta1, beta2, eps; /* Adam */
+    uint64_t seed;      /* parameter initialisation */
+    void *stream;       /* cudaStream_t */
+} cui_prescreen_desc;
+
+cui_status cui_prescreen_create(const cui_prescreen_desc *desc, cui_prescreen *out);
+void cui_prescreen_destroy(cui_prescreen p);
+/* number of parameters and of frames per feature row */
+cui_status cui_prescreen_info(cui_prescreen p, int64_t *n_params, int32_t *frames);
+/* features of `count` segments: dtilde_dev = [count][N/2 + 1] complex FP64
+ * (interleaved) data spectra d~_k, psd_dev = [N/2 + 1] FP64 */
+cui_status cui_prescreen_features(cui_prescreen p, const double *dtilde_dev, const double *psd_dev, int64_t count,
+                                  float *feat_dev);
+/* features of the segment last uploaded to `bank` (same N and sample rate) */
+cui_status cui_prescreen_bank_features(cui_prescreen p, cui_bank bank, float *feat_dev);
+/* region scores (logits) of `count` feature rows */
+cui_status cui_prescreen_scores(cui_prescreen p, const float *feat_dev, int64_t count, float *scores_dev);
+/* one Adam step on a batch; loss_host (nullable) receives the mean loss and
+ * then the call synchronises */
+cui_status cui_prescreen_train_step(cui_prescreen p, const float *feat_dev, const float *target_dev, int64_t count,
+                                    float *loss_host);
+/* mean gradient of the batch loss w.r.t. the parameters (n_params floats,
+ * device), without updating them */
+cui_status cui_prescreen_gradient(cui_prescreen p, const float *feat_dev, const float *target_dev, int64_t count,
+                                  float *grad_dev, float *loss_host);
+/* checkpoint / resume: FP32 parameters, Adam moments (host arrays of
+ * n_params floats, each nullable on get; m, v nullable on set = zero) and the
+ * step counter.  Synchronise. */
+cui_status cui_prescreen_get_state(cui_prescreen p, float *theta, float *m, float *v, int64_t *step);
+cui_status cui_prescreen_set_state(cui_prescreen p, const float *theta, const float *m, const float *v,
+                                   int64_t step);
+
 /* Allocation-free normalisation: sigma_t^2 = 4 df sum_k |h~_k|^2 / S_k of
  * `count` templates (m1[t], m2[t], host arrays) for the one-sided PSD psd_dev
  * (N/2 + 1 FP64 values in device memory, read on [k_lo, N/2)), written to

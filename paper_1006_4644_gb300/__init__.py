@@ -22,7 +22,7 @@ from . import _lib
 from ._lib import (CUI_PLAIN, CUI_PLAIN_FP64, CUI_PSI_FP64, CUI_STORE_BF16, PEAK_DTYPE, TRIGGER_DTYPE, CuiError,
                    cui_bank_desc)
 
-__all__ = ["Bank", "CuiError", "CUI_PSI_FP64", "CUI_STORE_BF16", "CUI_PLAIN", "CUI_PLAIN_FP64", "PEAK_DTYPE",
+__all__ = ["Bank", "Prescreen", "CuiError", "CUI_PSI_FP64", "CUI_STORE_BF16", "CUI_PLAIN", "CUI_PLAIN_FP64", "PEAK_DTYPE",
            "TRIGGER_DTYPE", "load"]
 
 load = _lib.load
@@ -159,6 +159,109 @@ class Bank:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             self._l.cui_bank_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Prescreen:
+    """The learned region prescreen (cui_prescreen_*): whitened band-power
+    features, a conv1d + MLP scorer, and its training on the GPU.  Device
+    arrays are torch tensors (float32 features [count, bands, frames], targets
+    and scores [count, regions]; complex128 data spectra [count, n/2 + 1])."""
+
+    def __init__(self, *, n: int, fs: float, f_low: float, bands: int = 8, frame: int = 512, regions: int = 100,
+                 max_batch: int = 256, lr: float = 1e-3, betas=(0.9, 0.999), eps: float = 1e-8, seed: int = 1,
+                 stream=None):
+        self._l = _lib.load_prescreen(_lib.load())
+        d = _lib.cui_prescreen_desc()
+        d.n, d.sample_rate, d.f_low, d.bands, d.frame, d.regions = int(n), float(fs), float(f_low), bands, frame, regions
+        d.max_batch, d.lr, d.beta1, d.beta2, d.eps, d.seed = max_batch, lr, betas[0], betas[1], eps, int(seed)
+        d.stream = _current_stream() if stream is None else int(stream)
+        self.desc = d
+        h = C.c_void_p()
+        _lib.check(self._l.cui_prescreen_create(C.byref(d), C.byref(h)), "cui_prescreen_create")
+        self._h = h
+        npar, frames = C.c_int64(), C.c_int32()
+        _lib.check(self._l.cui_prescreen_info(h, C.byref(npar), C.byref(frames)), "cui_prescreen_info")
+        self.n_params, self.frames, self.bands, self.regions = npar.value, frames.value, bands, regions
+
+    def features(self, dtilde_dev, psd_dev, out_dev):
+        count = dtilde_dev.shape[0] if dtilde_dev.dim() == 2 else 1
+        _lib.check(self._l.cui_prescreen_features(self._h, dtilde_dev.data_ptr(), psd_dev.data_ptr(), count,
+                                                  out_dev.data_ptr()), "cui_prescreen_features")
+
+    def bank_features(self, bank: "Bank", out_dev):
+        _lib.check(self._l.cui_prescreen_bank_features(self._h, bank._h, out_dev.data_ptr()),
+                   "cui_prescreen_bank_features")
+
+    def scores(self, feat_dev, out_dev):
+        _lib.check(self._l.cui_prescreen_scores(self._h, feat_dev.data_ptr(), feat_dev.shape[0], out_dev.data_ptr()),
+                   "cui_prescreen_scores")
+
+    def train_step(self, feat_dev, target_dev, want_loss: bool = True):
+        loss = C.c_float()
+        _lib.check(self._l.cui_prescreen_train_step(self._h, feat_dev.data_ptr(), target_dev.data_ptr(),
+                                                    feat_dev.shape[0], C.byref(loss) if want_loss else None),
+                   "cui_prescreen_train_step")
+        return loss.value if want_loss else None
+
+    def gradient(self, feat_dev, target_dev, grad_dev):
+        loss = C.c_float()
+        _lib.check(self._l.cui_prescreen_gradient(self._h, feat_dev.data_ptr(), target_dev.data_ptr(),
+                                                  feat_dev.shape[0], grad_dev.data_ptr(), C.byref(loss)),
+                   "cui_prescreen_gradient")
+        return loss.value
+
+    def get_state(self):
+        th, m, v = (np.zeros(self.n_params, dtype=np.float32) for _ in range(3))
+        st = C.c_int64()
+        _lib.check(self._l.cui_prescreen_get_state(self._h, th.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                                   C.byref(st)), "cui_prescreen_get_state")
+        return th, m, v, st.value
+
+    def set_state(self, theta, m=None, v=None, step: int = 0):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        mm = None if m is None else np.ascontiguousarray(m, dtype=np.float32)
+        vv = None if v is None else np.ascontiguousarray(v, dtype=np.float32)
+        _lib.check(self._l.cui_prescreen_set_state(self._h, th.ctypes.data, None if mm is None else mm.ctypes.data,
+                                                   None if vv is None else vv.ctypes.data, int(step)),
+                   "cui_prescreen_set_state")
+
+    def save(self, path: str):
+        """Checkpoint: JSON header line, then parameters, Adam moments (FP32)."""
+        import json
+
+        th, m, v, st = self.get_state()
+        hdr = {"n_params": self.n_params, "step": st, "bands": self.bands, "frames": self.frames,
+               "regions": self.regions, "n": self.desc.n, "frame": self.desc.frame}
+        with open(path, "wb") as fh:
+            fh.write((json.dumps(hdr) + "\n").encode())
+            fh.write(th.tobytes() + m.tobytes() + v.tobytes())
+
+    def load(self, path: str):
+        import json
+
+        with open(path, "rb") as fh:
+            hdr = json.loads(fh.readline())
+            if hdr["n_params"] != self.n_params:
+                raise ValueError("checkpoint does not match this network")
+            a = np.frombuffer(fh.read(), dtype=np.float32).reshape(3, self.n_params)
+        self.set_state(a[0], a[1], a[2], hdr["step"])
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._l.cui_prescreen_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

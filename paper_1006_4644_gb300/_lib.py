@@ -97,3 +97,30 @@ def check(status: int, where: str):
     if status != CUI_OK:
         raise CuiError(status, where, load().cui_last_error().decode())
     return status
+
+
+class cui_prescreen_desc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sample_rate", C.c_double), ("f_low", C.c_double), ("bands", C.c_int32),
+                ("frame", C.c_int32), ("regions", C.c_int32), ("max_batch", C.c_int32), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64),
+                ("stream", C.c_void_p)]
+
+
+def load_prescreen(lib):
+    vp = C.c_void_p
+    lib.cui_prescreen_create.argtypes = [C.POINTER(cui_prescreen_desc), C.POINTER(vp)]
+    lib.cui_prescreen_destroy.argtypes = [vp]
+    lib.cui_prescreen_destroy.restype = None
+    lib.cui_prescreen_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+    lib.cui_prescreen_features.argtypes = [vp, vp, vp, C.c_int64, vp]
+    lib.cui_prescreen_bank_features.argtypes = [vp, vp, vp]
+    lib.cui_prescreen_scores.argtypes = [vp, vp, C.c_int64, vp]
+    lib.cui_prescreen_train_step.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(C.c_float)]
+    lib.cui_prescreen_gradient.argtypes = [vp, vp, vp, C.c_int64, vp, C.POINTER(C.c_float)]
+    lib.cui_prescreen_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_int64)]
+    lib.cui_prescreen_set_state.argtypes = [vp, vp, vp, vp, C.c_int64]
+    for name in ("cui_prescreen_create", "cui_prescreen_info", "cui_prescreen_features", "cui_prescreen_bank_features",
+                 "cui_prescreen_scores", "cui_prescreen_train_step", "cui_prescreen_gradient",
+                 "cui_prescreen_get_state", "cui_prescreen_set_state"):
+        getattr(lib, name).restype = C.c_int
+    return lib

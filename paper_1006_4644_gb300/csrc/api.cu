@@ -162,6 +162,7 @@ struct cui_bank_s {
     // segment
     double *d_strain = nullptr, *d_psd = nullptr, *d_amp = nullptr, *d_prefix = nullptr, *d_scan = nullptr;
     double2 *d_fa = nullptr, *d_fb = nullptr;
+    const double2 *d_X = nullptr; // which of d_fa / d_fb holds the segment transform
     float2 *d_wbar = nullptr;
     void *d_dS = nullptr;
     SegScales *d_scales = nullptr;
@@ -203,7 +204,17 @@ struct cui_bank_s {
 namespace cui {
 std::atomic<long long> g_launches{0};
 void set_last_error(const char *msg) { g_err = msg; }
+
+bool bank_segment_spectrum(cui_bank b, const double2 **X, const double **psd, int64_t *n, double *fs)
+{
+    if (!b || !b->have_segment || !b->d_X) return false;
+    *X = b->d_X;
+    *psd = b->d_psd;
+    *n = b->n;
+    *fs = b->desc.sample_rate;
+    return true;
 }
+} // namespace cui
 
 namespace {
 const char *const kGroups[] = {"segment", "pass1", "pass2", "finalize", "plain"};
@@ -492,6 +503,7 @@ extern "C" cui_status cui_segment_upload(cui_bank b, const double *strain, int64
     launch_real_to_complex(b->d_strain, b->d_fa, b->n, s);
     double2 *X = nullptr;
     launch_fft_passes_f64(b->d_fa, b->d_fb, b->log2n, -1, b->tw, s, &X);
+    b->d_X = X;
     launch_weighted_data(X, b->d_psd, b->d_amp, b->n, b->k_low, b->desc.sample_rate, b->d_scales, b->d_wbar,
                          b->d_dS, b->plain_fp64, s);
     launch_prefix(b->d_psd, b->d_amp, b->n, b->k_low, b->d_prefix, b->d_scan, s);

@@ -47,8 +47,9 @@ struct Twiddles {
 void launch_twiddle_tables(const Twiddles &t, cudaStream_t s);
 void launch_fft_passes_f64(double2 *a, double2 *b, int log2n, int sign, const Twiddles &tw, cudaStream_t s,
                            double2 **result);
+// batch transforms of length 2^log2n stored back to back (grid rows)
 void launch_fft_passes_f32(float2 *a, float2 *b, int log2n, int sign, const Twiddles &tw, cudaStream_t s,
-                           float2 **result);
+                           float2 **result, int batch = 1);
 void launch_real_to_complex(const double *d, double2 *out, int64_t n, cudaStream_t s);
 void launch_amp_table(double *amp, int64_t nhalf, cudaStream_t s);
 void launch_weighted_data(const double2 *X, const double *psd, const double *amp, int64_t n, int k_low,
@@ -134,5 +135,10 @@ struct PlainArgs {
     bool fp64;
 };
 cudaError_t launch_plain_template(const PlainArgs &a, int t, cudaStream_t s);
+
+// ------------------------------------------------------------------ api.cu --
+// The uploaded segment's unnormalised FP64 transform X_k (k < N), its PSD,
+// N and the sample rate; false if no segment has been uploaded.
+bool bank_segment_spectrum(cui_bank b, const double2 **X, const double **psd, int64_t *n, double *fs);
 
 } // namespace cui

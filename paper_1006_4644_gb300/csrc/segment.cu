@@ -37,6 +37,8 @@ __global__ void __launch_bounds__(256) k_stockham(const cpx_t<Rl> *__restrict__ 
     const int64_t q = L / R;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= q) return;
+    in += (int64_t)blockIdx.y * L; // one transform per grid row
+    out += (int64_t)blockIdx.y * L;
     C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = in[j + r * q];
@@ -54,10 +56,10 @@ __global__ void __launch_bounds__(256) k_stockham(const cpx_t<Rl> *__restrict__ 
 
 template <typename Rl, int SIGN>
 static void stage(const cpx_t<Rl> *in, cpx_t<Rl> *out, int64_t L, int64_t Ns, int R, const TwTab<Rl> &tw,
-                  cudaStream_t s)
+                  cudaStream_t s, int batch)
 {
     const int64_t q = L / R;
-    const unsigned blocks = (unsigned)((q + 255) / 256);
+    const dim3 blocks((unsigned)((q + 255) / 256), (unsigned)batch);
     int lg = 0;
     while ((int64_t(1) << lg) < Ns * R) ++lg;
     const int lshift = tw.log2n - lg;
@@ -74,7 +76,7 @@ static void stage(const cpx_t<Rl> *in, cpx_t<Rl> *out, int64_t L, int64_t Ns, in
 // multiple of 4) then radix-16 stages, ping-ponging between a and b.
 template <typename Rl>
 static void fft_passes(cpx_t<Rl> *a, cpx_t<Rl> *b, int log2n, int sign, const TwTab<Rl> &tw, cudaStream_t s,
-                       cpx_t<Rl> **result)
+                       cpx_t<Rl> **result, int batch = 1)
 {
     const int64_t L = int64_t(1) << log2n;
     int64_t Ns = 1;
@@ -85,8 +87,8 @@ static void fft_passes(cpx_t<Rl> *a, cpx_t<Rl> *b, int log2n, int sign, const Tw
         int lr = rem ? rem : 4;
         rem = 0;
         int R = 1 << lr;
-        if (sign > 0) stage<Rl, +1>(src, dst, L, Ns, R, tw, s);
-        else stage<Rl, -1>(src, dst, L, Ns, R, tw, s);
+        if (sign > 0) stage<Rl, +1>(src, dst, L, Ns, R, tw, s, batch);
+        else stage<Rl, -1>(src, dst, L, Ns, R, tw, s, batch);
         Ns *= R;
         left -= lr;
         cpx_t<Rl> *t = src;
@@ -102,9 +104,9 @@ void launch_fft_passes_f64(double2 *a, double2 *b, int log2n, int sign, const Tw
     fft_passes<double>(a, b, log2n, sign, TwTab<double>{tw.lo64, tw.hi64, tw.shift, tw.log2n}, s, result);
 }
 void launch_fft_passes_f32(float2 *a, float2 *b, int log2n, int sign, const Twiddles &tw, cudaStream_t s,
-                           float2 **result)
+                           float2 **result, int batch)
 {
-    fft_passes<float>(a, b, log2n, sign, TwTab<float>{tw.lo32, tw.hi32, tw.shift, tw.log2n}, s, result);
+    fft_passes<float>(a, b, log2n, sign, TwTab<float>{tw.lo32, tw.hi32, tw.shift, tw.log2n}, s, result, batch);
 }
 
 // lo[i] = exp(2 pi i i / 2^log2n), hi[i] = exp(2 pi i (i << shift) / 2^log2n), in FP64 and FP32

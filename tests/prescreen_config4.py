@@ -1,0 +1,200 @@
+"""Evaluation of the learned prescreen on the stated prescreen workload (run on
+a GPU machine; not collected by pytest):
+
+    python tests/prescreen_config4.py [--train 200000] [--test 1000] [--epochs 6]
+
+The network is trained on the GPU with oracle-made injections (one per 16 s
+segment, N = 2^16 at 4096 Hz, SNR uniform in [6, 20], masses log-uniform in
+[1, 25] Msun, 3.5PN, f_low 20 Hz), labelled with the region (1 of 100
+equal-count chirp-mass groups of the 10^4-template bank) of the injected
+chirp mass.  On held-out segments the exhaustive bank is compared with
+filtering only the top-K scored regions: K* is the smallest K with zero missed
+injections among those the exhaustive bank detects at rho >= 8 (a miss: no
+template of the top-K regions reaches rho >= 8 within 1 s of the injection),
+and the speedup is the exhaustive time over prescreen + top-K* time.  Prints
+one JSON report; the same K* for an unranked (random) region order is the
+baseline without the network.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+from oracle import prescreen as ops  # noqa: E402
+from prescreen_data import make_segments_mp  # noqa: E402
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=200_000)
+    ap.add_argument("--test", type=int, default=1000)
+    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args()
+
+    import multiprocessing as mp
+
+    # the oracle's worker processes start (spawn) before the first GPU call
+    pool = mp.get_context("spawn").Pool(len(os.sched_getaffinity(0)))
+
+    import torch
+
+    from paper_1006_4644_gb300 import Bank, Prescreen, build
+    from paper_1006_4644_gb300.regions import ranked_order
+
+    build.build()
+    n, fs, f_low, R, W = 1 << 16, 4096.0, 20.0, 100, 4096
+    psd = synth.psd_onesided(n, fs)
+    bankw = synth.WORKLOADS["seg256s_bank10k_pn35"]
+    m1, m2 = bankw.masses()
+    groups, bounds = ops.regions_of_bank(m1, m2, R)
+    region_of_tmpl = np.empty(len(m1), dtype=np.int64)
+    for r, g in enumerate(groups):
+        region_of_tmpl[g] = r
+    ps_ = psd.copy()
+    ps_[0] = 1.0
+    psd_d = torch.from_numpy(ps_).cuda()
+    rep = {"n": n, "templates": len(m1), "regions": R, "train": args.train, "test": args.test, "epochs": args.epochs}
+
+    with Prescreen(n=n, fs=fs, f_low=f_low, bands=8, frame=512, regions=R, max_batch=args.batch, lr=args.lr,
+                   seed=1) as p:
+
+        def feats(start, count, keep_meta=False):
+            X, Y, M, D = [], [], [], []
+            for s0 in range(start, start + count, 2048):
+                d, y, meta = make_segments_mp(4, s0, min(2048, start + count - s0), n, fs, f_low, psd, bounds, R,
+                                              pool=pool)
+                out = torch.zeros((len(d), 8, p.frames), dtype=torch.float32, device="cuda")
+                p.features(torch.from_numpy(d).cuda(), psd_d, out)
+                X.append(out)
+                Y.append(torch.from_numpy(y).cuda())
+                M += meta
+                if keep_meta:
+                    D.append(d)
+            return torch.cat(X), torch.cat(Y), M, (np.concatenate(D) if keep_meta else None)
+
+        t0 = time.perf_counter()
+        xtr, ytr, _, _ = feats(0, args.train)
+        rep["data_s"] = time.perf_counter() - t0
+        mu, sd = xtr.mean(dim=(0, 2), keepdim=True), xtr.std(dim=(0, 2), keepdim=True)
+        xtr = ((xtr - mu) / sd).contiguous()
+        g = torch.Generator(device="cpu").manual_seed(0)
+        t0 = time.perf_counter()
+        losses = []
+        for epoch in range(args.epochs):
+            perm = torch.randperm(len(xtr), generator=g).cuda()
+            tot, nb = 0.0, 0
+            for i in range(0, len(xtr) - args.batch + 1, args.batch):
+                idx = perm[i:i + args.batch]
+                last = i + 2 * args.batch > len(xtr)
+                loss = p.train_step(xtr[idx].contiguous(), ytr[idx].contiguous(), want_loss=last)
+                if last:
+                    tot, nb = loss, 1
+            losses.append(tot / max(nb, 1))
+        torch.cuda.synchronize()
+        rep["train_s"] = time.perf_counter() - t0
+        rep["loss_by_epoch"] = losses
+
+        xte, yte, meta, dte = feats(10_000_000, args.test, keep_meta=True)
+        xte = ((xte - mu) / sd).contiguous()
+        scores = torch.zeros((len(xte), R), dtype=torch.float32, device="cuda")
+        p.scores(xte, scores)
+        sc = scores.cpu().numpy()
+        true = yte.argmax(dim=1).cpu().numpy()
+        rep["recall_at"] = {k: float(np.mean([t in np.argsort(-s)[:k] for t, s in zip(true, sc)]))
+                            for k in (1, 5, 10, 20, 50)}
+
+        # exhaustive bank on every held-out segment: region maxima of rho near the injection
+        rng = np.random.default_rng(0)
+        k_net, k_rand, detectable = [], [], 0
+        with Bank(m1, m2, n=n, fs=fs, f_low=f_low, pn_x2=7, snr_threshold=6.0, window=W) as bank:
+            for i, mt in enumerate(meta):
+                strain = synth.strain_from_spectrum(dte[i], n, fs)
+                bank.upload(strain, psd)
+                bank.filter()
+                tr, _ = bank.triggers()
+                dist = np.abs(tr["sample"] - mt["j0"])
+                dist = np.minimum(dist, n - dist)
+                near = tr[dist <= W]
+                reg_max = np.zeros(R)
+                if len(near):
+                    np.maximum.at(reg_max, region_of_tmpl[near["tmpl"]], near["snr"])
+                if reg_max.max() < 8.0:
+                    continue
+                detectable += 1
+                hit = reg_max >= 8.0
+                k_net.append(int(np.argmax(hit[np.argsort(-sc[i], kind="stable")])) + 1)
+                k_rand.append(int(np.argmax(hit[rng.permutation(R)])) + 1)
+            rep["detectable"] = detectable
+            k_star = int(max(k_net)) if k_net else R
+            rep["K_star"] = k_star
+            rep["K_star_random_order"] = int(max(k_rand)) if k_rand else R
+            rep["K_median"] = float(np.median(k_net)) if k_net else None
+            rep["K_median_random_order"] = float(np.median(k_rand)) if k_rand else None
+            # regions needed to find 99 % / 95 % of the detectable injections
+            for q in (99, 95):
+                rep[f"K_{q}pct"] = int(np.ceil(np.percentile(k_net, q))) if k_net else R
+                rep[f"K_{q}pct_random_order"] = int(np.ceil(np.percentile(k_rand, q))) if k_rand else R
+
+            # timing on a few held-out segments: exhaustive vs prescreen + top-K*
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            stream = torch.cuda.current_stream()
+            feat1 = torch.zeros((1, 8, p.frames), dtype=torch.float32, device="cuda")
+            sc1 = torch.zeros((1, R), dtype=torch.float32, device="cuda")
+            t_ex, t_ps, reps = 0.0, 0.0, 8
+            for i in range(reps):
+                bank.upload(synth.strain_from_spectrum(dte[i], n, fs), psd)
+                torch.cuda.synchronize()
+                ev[0].record(stream)
+                bank.filter()
+                ev[1].record(stream)
+                p.bank_features(bank, feat1)
+                feat_n = ((feat1 - mu) / sd).contiguous()
+                p.scores(feat_n, sc1)
+                order = ranked_order(sc1.cpu().numpy()[0], groups, k_star)
+                bank.filter(order)
+                ev[2].record(stream)
+                torch.cuda.synchronize()
+                t_ex += ev[0].elapsed_time(ev[1])
+                t_ps += ev[1].elapsed_time(ev[2])
+            rep["exhaustive_ms"] = t_ex / reps
+            rep["prescreen_plus_topK_ms"] = t_ps / reps
+            rep["speedup"] = t_ex / t_ps
+            # the same timing at the 99 % and 95 % points (misses allowed)
+            for q in (99, 95):
+                order = ranked_order(np.zeros(R), groups, rep[f"K_{q}pct"])
+                bank.upload(synth.strain_from_spectrum(dte[0], n, fs), psd)
+                torch.cuda.synchronize()
+                ev[0].record(stream)
+                for _ in range(reps):
+                    p.bank_features(bank, feat1)
+                    p.scores(((feat1 - mu) / sd).contiguous(), sc1)
+                    bank.filter(order)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                rep[f"speedup_at_{q}pct"] = (t_ex / reps) / (ev[0].elapsed_time(ev[1]) / reps)
+    pool.close()
+    pool.join()
+    line = json.dumps(rep)
+    print(line)
+    if args.out:
+        with open(args.out, "w") as fh:
+            fh.write(line + "\n")
+
+
+if __name__ == "__main__":
+    main()
