@@ -259,24 +259,34 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    bank.trace_read()
-    bank.trace(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
+    lib = bank._l
+
+    def timed(steps, level):
+        """Time `steps` steps (L2 flushed between them, outside the intervals)
+        with library tracing at `level`: 1 keeps the captured-graph path and
+        counts its kernels, 2 launches directly and times every kernel group."""
+        bank.trace_read()
+        lib.cui_trace_enable(bank._h, level)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for a, b in ev:
-            flush.zero_()  # L2 flushed between steps, outside the timed interval
+            flush.zero_()
             a.record(stream)
             step()
             b.record(stream)
         torch.cuda.synchronize()
+        lib.cui_trace_enable(bank._h, 0)
+        return sum(a.elapsed_time(b) for a, b in ev), bank.trace_read()
+
     if world > 1:
         dist.barrier()
-    bank.trace(False)
-    trace = bank.trace_read()
-    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t_ms, calls = timed(args.steps, 1)
+        # the same steps once more with per-kernel events, for the roofline
+        _, trace = timed(args.steps, 2)
+    if world > 1:
+        dist.barrier()
+    launches = sum(v[0] for v in calls.values())
     if world > 1:
         tt = torch.tensor([t_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -286,7 +296,6 @@ def main():
     # roofline of the dominant kernel: algorithmic bytes = one write (pass 1)
     # or one read (pass 2) of the N-point complex64 spectrum per template
     per_tmpl = w.n * (4 if args.flags & 2 else 8)
-    launches = sum(v[0] for v in trace.values())
     p1 = trace.get("pass1", (0, 0, 0.0))
     p2 = trace.get("pass2", (0, 0, 0.0))
     dom, dv = ("pass2", p2) if p2[2] >= p1[2] else ("pass1", p1)

@@ -61,6 +61,7 @@ typedef enum {
 #define CUI_STORE_BF16  0x2u /* fused path: store the spectrum between FFT passes as bf16 pairs */
 #define CUI_PLAIN       0x4u /* per-template unfused path: generate, multiply, multi-pass FFT, detect */
 #define CUI_PLAIN_FP64  0x8u /* with CUI_PLAIN: template, product and FFT in FP64 (else FP32) */
+#define CUI_NO_GRAPH    0x10u /* fused path: launch kernels directly instead of replaying a captured CUDA graph */
 
 typedef struct cui_bank_s *cui_bank; /* opaque; owns every device buffer it allocates */
 
@@ -185,11 +186,14 @@ cui_status cui_bank_set_tuning(cui_bank bank, const cui_tuning *tuning);
  * Not in the paper: its kernels had no tunable tiling. */
 cui_status cui_bank_autotune(cui_bank bank, int32_t reps, cui_tuning *best, double *best_ms);
 
-/* Tracing.  With tracing on, every call records CUDA events on desc.stream
- * around each group of kernels it launches ("segment", "pass1", "pass2",
- * "finalize", "plain"); cui_trace_read synchronises, writes up to `capacity`
- * per-group totals (launches of this library's kernels, summed event time)
- * to host_out, the number of groups to *n, and clears the record.
+/* Tracing.  cui_trace_enable(bank, level): 0 off; 1 records CUDA events on
+ * desc.stream around each call's groups of kernels ("segment", "plain", and
+ * "graph" for the captured fused filter); 2 also times every fused kernel
+ * group ("pass1", "pass2", "finalize"), for which the fused filter launches
+ * its kernels directly instead of replaying its graph.  cui_trace_read
+ * synchronises, writes up to `capacity` per-group totals (launches of this
+ * library's kernels, summed event time) to host_out, the number of groups to
+ * *n, and clears the record.
  * Errors: CUI_ERR_ARG, CUI_ERR_CUDA.  Paper: the per-step timing information
  * of Sec. "GPU based detection pipeline performances and profiling". */
 typedef struct {

@@ -145,9 +145,11 @@ class Bank:
         _lib.check(self._l.cui_bank_autotune(self._h, int(reps), C.byref(tu), C.byref(ms)), "cui_bank_autotune")
         return tu.as_dict(), ms.value
 
-    def trace(self, on: bool = True):
-        """Record CUDA events around every kernel group of later calls."""
-        _lib.check(self._l.cui_trace_enable(self._h, int(bool(on))), "cui_trace_enable")
+    def trace(self, level: int = 1):
+        """Record CUDA events around the kernel groups of later calls: level 1
+        per call group (the fused filter stays one graph launch), level 2 per
+        fused kernel group (direct launches), 0 off."""
+        _lib.check(self._l.cui_trace_enable(self._h, int(level)), "cui_trace_enable")
 
     def trace_read(self) -> dict:
         """{group: (kernel launches, timed intervals, total ms)} since the last read."""

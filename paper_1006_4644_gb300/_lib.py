@@ -17,7 +17,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "cui.h")
 CUI_OK, CUI_ERR_ARG, CUI_ERR_CUDA, CUI_ERR_OOM, CUI_ERR_STATE, CUI_ERR_OVERFLOW, CUI_ERR_TIMEOUT = range(7)
 STATUS_NAMES = {0: "CUI_OK", 1: "CUI_ERR_ARG", 2: "CUI_ERR_CUDA", 3: "CUI_ERR_OOM", 4: "CUI_ERR_STATE",
                 5: "CUI_ERR_OVERFLOW", 6: "CUI_ERR_TIMEOUT"}
-CUI_PSI_FP64, CUI_STORE_BF16, CUI_PLAIN, CUI_PLAIN_FP64 = 0x1, 0x2, 0x4, 0x8
+CUI_PSI_FP64, CUI_STORE_BF16, CUI_PLAIN, CUI_PLAIN_FP64, CUI_NO_GRAPH = 0x1, 0x2, 0x4, 0x8, 0x10
 
 
 class cui_bank_desc(C.Structure):

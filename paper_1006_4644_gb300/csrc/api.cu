@@ -130,6 +130,19 @@ int exact_bound(double c0, int ccols, int64_t nh)
     return (int)std::min<double>(std::ceil(k), (double)std::min<int64_t>(nh, kExactMax));
 }
 
+// What a captured filter call depends on besides the buffers' contents.
+struct GraphKey {
+    int64_t count;
+    const int32_t *order;
+    const cui_peak *peaks;
+    int n1, ccols, rpc, batch;
+    bool operator==(const GraphKey &o) const
+    {
+        return count == o.count && order == o.order && peaks == o.peaks && n1 == o.n1 && ccols == o.ccols &&
+               rpc == o.rpc && batch == o.batch;
+    }
+};
+
 template <typename T> cudaError_t dalloc(T **p, size_t count)
 {
     *p = nullptr;
@@ -190,8 +203,13 @@ struct cui_bank_s {
     int32_t *d_order = nullptr;
     int64_t order_cap = 0;
     bool have_segment = false, have_peaks = false;
+    // CUDA graph of the last fused filter call and its signature
+    cudaStream_t cap_stream = nullptr;
+    GraphKey gkey = {};
+    cudaGraphExec_t gexec = nullptr;
+    long long glaunches = 0;
     // tracing: (group, start, stop, launches) per recorded interval
-    bool trace = false;
+    int trace = 0; // 0 off, 1 call groups, 2 every kernel group
     struct Mark {
         int group;
         cudaEvent_t a, b;
@@ -217,8 +235,8 @@ bool bank_segment_spectrum(cui_bank b, const double2 **X, const double **psd, in
 } // namespace cui
 
 namespace {
-const char *const kGroups[] = {"segment", "pass1", "pass2", "finalize", "plain"};
-constexpr int kNGroups = 5;
+const char *const kGroups[] = {"segment", "pass1", "pass2", "finalize", "plain", "graph"};
+constexpr int kNGroups = 6;
 
 cudaEvent_t take_event(cui_bank b)
 {
@@ -232,22 +250,25 @@ cudaEvent_t take_event(cui_bank b)
     return e;
 }
 
-// Opens a traced interval of `group` on the bank's stream; close() ends it.
+// Opens a traced interval of `group` on the bank's stream when the tracing
+// level is at least `level`; close() ends it.  Per-kernel groups use level 2,
+// at which the fused path launches directly (a graph could not hold events
+// of the bank's own stream).
 struct Span {
     cui_bank b;
     int group;
     cudaEvent_t a = nullptr;
     long long l0 = 0;
-    Span(cui_bank b_, int g) : b(b_), group(g)
+    Span(cui_bank b_, int g, int level = 1) : b(b_), group(g)
     {
-        if (!b->trace) return;
+        if (b->trace < level) return;
         a = take_event(b);
         l0 = g_launches.load();
         cudaEventRecord(a, b->stream);
     }
     void close()
     {
-        if (!b->trace || !a) return;
+        if (!a) return;
         cudaEvent_t e = take_event(b);
         cudaEventRecord(e, b->stream);
         b->marks.push_back({group, a, e, g_launches.load() - l0});
@@ -272,6 +293,8 @@ static void release(cui_bank b)
         cudaEventDestroy(m.b);
     }
     for (cudaEvent_t e : b->pool) cudaEventDestroy(e);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
 }
 
 extern "C" const char *cui_last_error(void) { return g_err.c_str(); }
@@ -283,6 +306,10 @@ static cudaError_t build_phase_tables(cui_bank b, int n1, int ccols)
     const cudaStream_t s = b->stream;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
+    if (b->gexec) { // the captured graph refers to the buffers replaced here
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
     for (void *p : {(void *)b->d_basis, (void *)b->d_basis_df, (void *)b->d_kex, (void *)b->d_gexact})
         if (p) cudaFree(p);
     b->d_basis = nullptr;
@@ -316,6 +343,10 @@ static cudaError_t configure_fused(cui_bank b, const cui_tuning &tu)
     const cudaStream_t s = b->stream;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
     if (b->d_y) cudaFree(b->d_y);
     if (b->d_win) cudaFree(b->d_win);
     b->d_y = nullptr;
@@ -351,7 +382,8 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
         return fail(CUI_ERR_ARG, "need 0 <= valid_lo <= valid_hi <= n");
     if (!std::isfinite(d.snr_threshold) || d.snr_threshold < 0) return fail(CUI_ERR_ARG, "snr_threshold must be >= 0");
     if (d.trigger_capacity < 0) return fail(CUI_ERR_ARG, "trigger_capacity must be >= 0");
-    if (d.flags & ~(CUI_PSI_FP64 | CUI_STORE_BF16 | CUI_PLAIN | CUI_PLAIN_FP64)) return fail(CUI_ERR_ARG, "unknown flags");
+    if (d.flags & ~(CUI_PSI_FP64 | CUI_STORE_BF16 | CUI_PLAIN | CUI_PLAIN_FP64 | CUI_NO_GRAPH))
+        return fail(CUI_ERR_ARG, "unknown flags");
     if (n_templates < 1 || n_templates > (int64_t(1) << 31) - 1) return fail(CUI_ERR_ARG, "n_templates out of range");
     for (int64_t i = 0; i < n_templates; ++i)
         if (!(m1[i] > 0) || !(m2[i] > 0) || !std::isfinite(m1[i]) || !std::isfinite(m2[i]))
@@ -426,6 +458,7 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     chk(dalloc(&b->d_trig, b->trig_cap));
     chk(dalloc(&b->d_trig_count, 1));
     chk(dalloc(&b->d_err, 1));
+    chk(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
     b->h_c0.resize(nt);
     for (int64_t t = 0; t < nt; ++t) b->h_c0[t] = coef[t * kNB];
     if (b->fused) {
@@ -549,6 +582,49 @@ static FusedArgs fused_args(cui_bank b, const int32_t *order, int64_t base)
     return a;
 }
 
+static FinalizeArgs finalize_args(cui_bank b, const int32_t *d_ord, cui_peak *pout)
+{
+    FinalizeArgs fa;
+    fa.order = d_ord;
+    fa.peak = b->d_peak;
+    fa.win = b->d_win;
+    fa.nwin = b->nwin;
+    fa.lo = b->desc.valid_lo;
+    fa.window = b->desc.window;
+    fa.peaks_out = pout;
+    fa.trig = b->d_trig;
+    fa.trig_cap = b->trig_cap;
+    fa.trig_count = b->d_trig_count;
+    fa.base = 0;
+    fa.count = 0;
+    return fa;
+}
+
+// The fused path's launches for `count` templates: per batch, pass 1,
+// pass 2 and the finalize kernels.
+static cudaError_t enqueue_fused(cui_bank b, const int32_t *d_ord, int64_t count, cui_peak *pout, cudaStream_t s)
+{
+    FinalizeArgs fa = finalize_args(b, d_ord, pout);
+    for (int64_t base = 0; base < count; base += b->batch) {
+        const int bc = (int)std::min<int64_t>(b->batch, count - base);
+        FusedArgs a = fused_args(b, d_ord, base);
+        cudaError_t e;
+        {
+            Span sp(b, 1, 2);
+            if ((e = launch_pass1(a, bc, s)) != cudaSuccess) return e;
+        }
+        {
+            Span sp(b, 2, 2);
+            if ((e = launch_pass2(a, bc, s)) != cudaSuccess) return e;
+        }
+        fa.base = base;
+        fa.count = bc;
+        Span sp(b, 3, 2);
+        if ((e = launch_finalize(fa, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 extern "C" cui_status cui_filter_bank(cui_bank b, const int32_t *order, int64_t count, cui_peak *peaks_dev)
 {
     if (!b) return fail(CUI_ERR_ARG, "bank is NULL");
@@ -575,37 +651,43 @@ extern "C" cui_status cui_filter_bank(cui_bank b, const int32_t *order, int64_t 
                            "order copy");
         d_ord = b->d_order;
     }
-    CUI_TRY(cudaMemsetAsync(b->d_trig_count, 0, sizeof(unsigned long long), s), "trigger reset");
     cui_peak *pout = peaks_dev ? peaks_dev : b->d_peaks;
-    FinalizeArgs fa;
-    fa.order = d_ord;
-    fa.peak = b->d_peak;
-    fa.nwin = b->nwin;
-    fa.lo = b->desc.valid_lo;
-    fa.window = b->desc.window;
-    fa.peaks_out = pout;
-    fa.trig = b->d_trig;
-    fa.trig_cap = b->trig_cap;
-    fa.trig_count = b->d_trig_count;
-    if (b->fused) {
-        fa.win = b->d_win;
-        for (int64_t base = 0; base < count; base += b->batch) {
-            const int bc = (int)std::min<int64_t>(b->batch, count - base);
-            FusedArgs a = fused_args(b, d_ord, base);
-            {
-                Span sp(b, 1);
-                CUI_TRY(launch_pass1(a, bc, s), "fused pass 1");
+    if (b->fused && b->trace < 2 && !(b->desc.flags & CUI_NO_GRAPH) && count > 0) {
+        // The whole call as one CUDA graph: captured once per signature on the
+        // bank's private stream, replayed on the caller's stream.
+        const GraphKey key = {count, d_ord, pout, b->n1, b->ccols, b->rpc, b->batch};
+        if (!b->gexec || !(b->gkey == key)) {
+            if (b->gexec) cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+            const long long l0 = g_launches.load();
+            CUI_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+            cudaError_t e1 = cudaMemsetAsync(b->d_trig_count, 0, sizeof(unsigned long long), b->cap_stream);
+            cudaError_t e2 = e1 == cudaSuccess ? enqueue_fused(b, d_ord, count, pout, b->cap_stream) : e1;
+            cudaGraph_t graph = nullptr;
+            cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &graph);
+            if (e2 != cudaSuccess || e3 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return cuda_fail(e2 != cudaSuccess ? e2 : e3, "graph capture");
             }
-            {
-                Span sp(b, 2);
-                CUI_TRY(launch_pass2(a, bc, s), "fused pass 2");
+            cudaError_t e4 = cudaGraphInstantiate(&b->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e4 != cudaSuccess) {
+                b->gexec = nullptr;
+                return cuda_fail(e4, "graph instantiate");
             }
-            fa.base = base;
-            fa.count = bc;
-            Span sp(b, 3);
-            CUI_TRY(launch_finalize(fa, s), "finalize");
+            b->gkey = key;
+            b->glaunches = g_launches.load() - l0;
+            g_launches.fetch_sub(b->glaunches); // counted when replayed
         }
+        Span sp(b, 5);
+        CUI_TRY(cudaGraphLaunch(b->gexec, s), "graph launch");
+        launched((int)b->glaunches);
+    } else if (b->fused) {
+        CUI_TRY(cudaMemsetAsync(b->d_trig_count, 0, sizeof(unsigned long long), s), "trigger reset");
+        CUI_TRY(enqueue_fused(b, d_ord, count, pout, s), "fused filter");
     } else {
+        CUI_TRY(cudaMemsetAsync(b->d_trig_count, 0, sizeof(unsigned long long), s), "trigger reset");
+        FinalizeArgs fa = finalize_args(b, d_ord, pout);
         PlainArgs a;
         a.mass = b->d_mass;
         a.khi = b->d_khi;
@@ -671,8 +753,8 @@ extern "C" cui_status cui_bank_autotune(cui_bank b, int32_t reps, cui_tuning *be
     if (!b->fused) return fail(CUI_ERR_STATE, "the bank runs the per-template path, which has no tiling");
     if (!b->have_segment) return fail(CUI_ERR_STATE, "autotuning times the uploaded segment: upload one first");
     const cudaStream_t s = b->stream;
-    const bool trace = b->trace;
-    b->trace = false;
+    const int trace = b->trace;
+    b->trace = 0;
     cudaEvent_t e0, e1;
     CUI_TRY(cudaEventCreate(&e0), "autotune events");
     CUI_TRY(cudaEventCreate(&e1), "autotune events");
@@ -720,7 +802,7 @@ extern "C" cui_status cui_bank_autotune(cui_bank b, int32_t reps, cui_tuning *be
 extern "C" cui_status cui_trace_enable(cui_bank b, int on)
 {
     if (!b) return fail(CUI_ERR_ARG, "bank is NULL");
-    b->trace = on != 0;
+    b->trace = on < 0 ? 0 : (on > 2 ? 2 : on);
     return CUI_OK;
 }
 

@@ -145,3 +145,25 @@ def test_small_segments_use_the_plain_path():
         tr, _ = b.triggers()
     rep = compare_bank(w, dt, psd, p, tr, range(w.n_templates), 0, w.n, 100, 6.0)
     assert rep.ok(), rep
+
+
+def test_graph_replay_matches_direct_launches(seg):
+    """cui_filter_bank replays a captured CUDA graph by default; results equal
+    the directly launched kernels, across calls that change the order's
+    contents (same buffer) and its length (new capture)."""
+    from paper_1006_4644_gb300 import _lib
+
+    strain, psd, _, _ = seg
+    orders = [None, [5, 0, 3], [1, 2, 4], [0, 1, 2, 3, 4, 5]]
+    res = {}
+    for flags in (0, _lib.CUI_NO_GRAPH):
+        with _bank(flags=flags, snr_threshold=4.0) as b:
+            b.upload(strain, psd)
+            out = []
+            for o in orders:
+                b.filter(order=o)
+                out.append((b.peaks().copy(), b.triggers()[0]))
+            res[flags] = out
+    for (pa, ta), (pb, tb) in zip(res[0], res[_lib.CUI_NO_GRAPH]):
+        assert np.array_equal(pa, pb)
+        assert np.array_equal(ta, tb)
