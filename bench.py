@@ -213,6 +213,7 @@ def main():
     ap.add_argument("--plain-templates", type=int, default=64)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--tuning", default=None, help="fixed tiling n1,ccols,rpc,batch (skips the autotuner)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -254,7 +255,12 @@ def main():
 
     # pick the tiling on this GPU (outside the timed region)
     bank.upload(strain_d, psd_d)
-    tuning, _ = bank.autotune(reps=2) if args.autotune else (bank.tuning(), None)
+    if args.tuning:
+        n1, cc, rpc, bt = (int(x) for x in args.tuning.split(","))
+        bank.set_tuning(n1=n1, ccols=cc, rpc=rpc, batch=bt)
+        tuning = bank.tuning()
+    else:
+        tuning, _ = bank.autotune(reps=2) if args.autotune else (bank.tuning(), None)
 
     for _ in range(args.warmup):
         step()

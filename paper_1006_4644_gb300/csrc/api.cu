@@ -491,7 +491,7 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
         cui_tuning tu;
         fused_default_tiling(b->log2n, &tu.n1, &tu.ccols, &tu.rpc);
         const int64_t per = b->n * ((d.flags & CUI_STORE_BF16) ? 4 : 8);
-        tu.batch = (int32_t)std::min<int64_t>(nt, std::max<int64_t>(1, std::min<int64_t>(4096, (1ll << 30) / per)));
+        tu.batch = (int32_t)std::min<int64_t>(nt, std::max<int64_t>(1, std::min<int64_t>(4096, (1ll << 31) / per)));
         chk(configure_fused(b, tu));
     } else {
         chk(cudaMemsetAsync(b->d_pwin, 0, sizeof(Slot) * std::max(1, b->nwin), s));

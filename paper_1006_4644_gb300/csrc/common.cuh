@@ -27,6 +27,54 @@ template <typename C> CUI_HD C cmulc(C a, C b) { return mk(a.x * b.x + a.y * b.y
 template <typename C, typename R> CUI_HD C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
 // multiply by sign * i  (i for SIGN = +1, -i for SIGN = -1)
 template <int SIGN, typename C> CUI_HD C mul_si(C a) { return SIGN > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x); }
+// a + sign * i * d and a - sign * i * d
+template <int SIGN, typename C> CUI_HD C add_si(C a, C d)
+{
+    return SIGN > 0 ? mk(a.x - d.y, a.y + d.x) : mk(a.x + d.y, a.y - d.x);
+}
+template <int SIGN, typename C> CUI_HD C sub_si(C a, C d)
+{
+    return SIGN > 0 ? mk(a.x + d.y, a.y - d.x) : mk(a.x - d.y, a.y + d.x);
+}
+
+// ------------------------------------------------- paired complex (f32x2) ---
+// Two independent complex numbers (lanes 0 and 1, e.g. two rows of one
+// transform) kept as a real pair and an imaginary pair, so that every add,
+// subtract and multiply of a transform is one packed FP32x2 instruction for
+// both lanes (sm_100 family).  Multiplying by +-i only exchanges the pairs.
+struct c2 {
+    float2 re, im;
+};
+
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as one fused multiply-add by -1 (exact product, one rounding)
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 f2neg(float2 a) { return __fmul2_rn(a, make_float2(-1.f, -1.f)); }
+__device__ __forceinline__ c2 operator+(c2 a, c2 b) { return {f2add(a.re, b.re), f2add(a.im, b.im)}; }
+__device__ __forceinline__ c2 operator-(c2 a, c2 b) { return {f2sub(a.re, b.re), f2sub(a.im, b.im)}; }
+// both lanes times the same complex w
+__device__ __forceinline__ c2 cmul(c2 a, float2 w)
+{
+    const float2 wx = make_float2(w.x, w.x), wy = make_float2(w.y, w.y), nwy = make_float2(-w.y, -w.y);
+    return {__ffma2_rn(a.im, nwy, __fmul2_rn(a.re, wx)), __ffma2_rn(a.im, wx, __fmul2_rn(a.re, wy))};
+}
+template <int SIGN> __device__ __forceinline__ c2 mul_si(c2 a)
+{
+    return SIGN > 0 ? c2{f2neg(a.im), a.re} : c2{a.im, f2neg(a.re)};
+}
+template <int SIGN> __device__ __forceinline__ c2 add_si(c2 a, c2 d)
+{
+    return SIGN > 0 ? c2{f2sub(a.re, d.im), f2add(a.im, d.re)} : c2{f2add(a.re, d.im), f2sub(a.im, d.re)};
+}
+template <int SIGN> __device__ __forceinline__ c2 sub_si(c2 a, c2 d)
+{
+    return SIGN > 0 ? c2{f2add(a.re, d.im), f2sub(a.im, d.re)} : c2{f2sub(a.re, d.im), f2add(a.im, d.re)};
+}
+
+// real type of a complex type
+template <typename C> struct real_of { using T = decltype(C{}.x); };
+template <> struct real_of<c2> { using T = float; };
+template <typename C> using real_t = typename real_of<C>::T;
 
 // ------------------------------------------------------ in-register DFTs ---
 // y_k = sum_r v_r exp(SIGN 2 pi i r k / R), in place, natural order.
@@ -39,11 +87,11 @@ template <int SIGN, typename C> CUI_HD void dft2(C &a, C &b)
 
 template <int SIGN, typename C> CUI_HD void dft4(C &v0, C &v1, C &v2, C &v3)
 {
-    C a0 = v0 + v2, a1 = v0 - v2, a2 = v1 + v3, a3 = mul_si<SIGN>(v1 - v3);
+    const C a0 = v0 + v2, a1 = v0 - v2, a2 = v1 + v3, d = v1 - v3;
     v0 = a0 + a2;
     v2 = a0 - a2;
-    v1 = a1 + a3;
-    v3 = a1 - a3;
+    v1 = add_si<SIGN>(a1, d);
+    v3 = sub_si<SIGN>(a1, d);
 }
 
 template <typename R> struct k16 {
@@ -63,7 +111,7 @@ template <int SIGN, typename C, typename R> CUI_HD C w8(C a, int m)
 
 template <int SIGN, typename C> CUI_HD void dft8(C *v)
 {
-    using R = decltype(v[0].x);
+    using R = real_t<C>;
     // r = r1 + 2 r2: DFT4 over r2 for r1 = 0, 1; twiddle w8^(r1 k2); DFT2 over r1.
     dft4<SIGN>(v[0], v[2], v[4], v[6]);
     dft4<SIGN>(v[1], v[3], v[5], v[7]);
@@ -83,7 +131,7 @@ template <int SIGN, typename C> CUI_HD void dft8(C *v)
 
 template <int SIGN, typename C> CUI_HD void dft16(C *v)
 {
-    using R = decltype(v[0].x);
+    using R = real_t<C>;
     // r = r1 + 4 r2: DFT4 over r2 for each r1, twiddle w16^(r1 k2), DFT4 over r1.
 #pragma unroll
     for (int r1 = 0; r1 < 4; ++r1) dft4<SIGN>(v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12]);
@@ -123,11 +171,11 @@ template <int R, int SIGN, typename C> CUI_HD void dft(C *v)
 // DFT4 of (a, b, 0, 0): inputs v2, v3 are not read.
 template <int SIGN, typename C> CUI_HD void dft4_lo2(C &v0, C &v1, C &v2, C &v3)
 {
-    const C a = v0, b = v1, sb = mul_si<SIGN>(b);
+    const C a = v0, b = v1;
     v0 = a + b;
-    v1 = a + sb;
+    v1 = add_si<SIGN>(a, b);
     v2 = a - b;
-    v3 = a - sb;
+    v3 = sub_si<SIGN>(a, b);
 }
 
 // DFT_R of v when only v[0 .. NZ) can be nonzero (NZ a power of two <= R):
@@ -135,7 +183,7 @@ template <int SIGN, typename C> CUI_HD void dft4_lo2(C &v0, C &v1, C &v2, C &v3)
 // inputs v[NZ ..) are never read.  Same decompositions as dft8 / dft16.
 template <int NZ, int SIGN, typename C> CUI_HD void dft8_nz(C *v)
 {
-    using R = decltype(v[0].x);
+    using R = real_t<C>;
     if constexpr (NZ >= 8) {
         dft8<SIGN>(v);
     } else if constexpr (NZ == 1) {
@@ -166,7 +214,7 @@ template <int NZ, int SIGN, typename C> CUI_HD void dft8_nz(C *v)
 
 template <int NZ, int SIGN, typename C> CUI_HD void dft16_nz(C *v)
 {
-    using R = decltype(v[0].x);
+    using R = real_t<C>;
     if constexpr (NZ >= 16) {
         dft16<SIGN>(v);
     } else if constexpr (NZ == 1) {

@@ -21,6 +21,8 @@
 // sincos of an argument already in [-pi, pi) and one complex product.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace cui {
@@ -44,6 +46,43 @@ template <> __device__ __forceinline__ float2 ld_c<float2>(const float2 *p) { re
 template <> __device__ __forceinline__ float2 ld_c<__nv_bfloat162>(const __nv_bfloat162 *p)
 {
     return __bfloat1622float2(*p);
+}
+
+// Paired layout of Y: rows c and c + n1/2 of one template interleaved at each
+// column b as (re_c, re_c', im_c, im_c'), which pass 2 loads straight into a
+// c2 (the two rows are its two lanes).  Row pair c holds n2 such entries.
+template <typename ST> struct pair_of;
+template <> struct pair_of<float2> { using T = float4; };
+template <> struct pair_of<__nv_bfloat162> { using T = uint2; };
+template <typename ST> using pair_t = typename pair_of<ST>::T;
+
+template <typename ST> __device__ __forceinline__ void st_pair(pair_t<ST> *p, float2 lo, float2 hi);
+template <> __device__ __forceinline__ void st_pair<float2>(float4 *p, float2 lo, float2 hi)
+{
+    *p = make_float4(lo.x, hi.x, lo.y, hi.y);
+}
+template <> __device__ __forceinline__ void st_pair<__nv_bfloat162>(uint2 *p, float2 lo, float2 hi)
+{
+    const __nv_bfloat162 re = __floats2bfloat162_rn(lo.x, hi.x), im = __floats2bfloat162_rn(lo.y, hi.y);
+    *p = make_uint2(*(const unsigned *)&re, *(const unsigned *)&im);
+}
+template <typename ST> __device__ __forceinline__ c2 ld_pair(const pair_t<ST> *p);
+template <> __device__ __forceinline__ c2 ld_pair<float2>(const float4 *p)
+{
+    const float4 q = *p;
+    return {make_float2(q.x, q.y), make_float2(q.z, q.w)};
+}
+template <> __device__ __forceinline__ c2 ld_pair<__nv_bfloat162>(const uint2 *p)
+{
+    const uint2 q = *p;
+    return {__bfloat1622float2(*(const __nv_bfloat162 *)&q.x), __bfloat1622float2(*(const __nv_bfloat162 *)&q.y)};
+}
+
+// element idx of template-slice `base`, as one complex (unpaired) or one row pair
+template <typename ST, bool PAIR> __device__ __forceinline__ auto ld_y(const char *base, size_t idx)
+{
+    if constexpr (PAIR) return ld_pair<ST>((const pair_t<ST> *)base + idx);
+    else return ld_c<ST>((const ST *)base + idx);
 }
 
 // exp(2 pi i m / d) for 0 <= m < d, accurate to ~1 ulp.
@@ -183,8 +222,9 @@ __device__ __forceinline__ void p1_stage0(float2 *v, const FusedArgs &p, const f
 // Grid (n2 / C, ceil(B / G)).  A CTA owns C columns of n1 = R0 * R1 rows and
 // runs G templates through them, so the twiddles that depend only on the
 // position (the stage-1 table and the inter-pass factors exp(2 pi i b c / N),
-// kept in registers) are computed once per CTA.
-template <int N1, int R0, int R1, int C, int G, typename ST>
+// kept in registers) are computed once per CTA.  PAIR selects the paired
+// layout of Y (rows c and c + n1/2 interleaved), else rows are stored whole.
+template <int N1, int R0, int R1, int C, int G, typename ST, bool PAIR>
 __global__ void __launch_bounds__(C *N1 / 16, (C * N1 / 16 <= 512 ? 2 : 1)) k_pass1(const FusedArgs p, int count)
 {
     constexpr int NT = C * N1 / 16;
@@ -245,7 +285,7 @@ __global__ void __launch_bounds__(C *N1 / 16, (C * N1 / 16 <= 512 ? 2 : 1)) k_pa
         __syncthreads();
 
         // stage 1 (last): radix R1 over sub-transforms of size R0; times exp(2 pi i b c / N)
-        ST *yout = (ST *)p.ywork + (size_t)y * (size_t)N;
+        char *yslice = (char *)p.ywork + (size_t)y * (size_t)N * sizeof(ST);
 #pragma unroll
         for (int i = 0; i < T1; ++i) {
             const int j = jt + i * (N1 / 16);
@@ -257,29 +297,54 @@ __global__ void __launch_bounds__(C *N1 / 16, (C * N1 / 16 <= 512 ? 2 : 1)) k_pa
             for (int r = 1; r < R1; ++r) u[r] = cmul(u[r], tw[jm * r]);
             dft<R1, +1>(u);
             float2 w = ipb[i];
+            if constexpr (PAIR) {
 #pragma unroll
-            for (int r = 0; r < R1; ++r) {
-                const int c = j + r * (N1 / R1);
-                st_c<ST>(yout + (size_t)c * n2 + bcol, cmul(u[r], w));
-                w = cmul(w, ips);
+                for (int r = 0; r < R1; ++r) {
+                    u[r] = cmul(u[r], w);
+                    w = cmul(w, ips);
+                }
+                // output c = j + r N1/R1 and its partner c + N1/2 (r + R1/2) form one row pair
+#pragma unroll
+                for (int r = 0; r < R1 / 2; ++r) {
+                    const int c = j + r * (N1 / R1);
+                    st_pair<ST>((pair_t<ST> *)yslice + (size_t)c * n2 + bcol, u[r], u[r + R1 / 2]);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R1; ++r) {
+                    const int c = j + r * (N1 / R1);
+                    st_c<ST>((ST *)yslice + (size_t)c * n2 + bcol, cmul(u[r], w));
+                    w = cmul(w, ips);
+                }
             }
         }
     }
 }
 
 // ---------------------------------------------------------------- pass 2 ---
-// One spare complex slot every 16 keeps the stride-16 stores conflict-free.
+// One spare slot every 16 keeps the stride-16 stores conflict-free.
 __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
 
+// Elements of pass 2 are one complex value (float2) or, in the paired layout,
+// the same position of two rows (c2, one row per lane).
+template <typename E> constexpr int lanes_of = 1;
+template <> constexpr int lanes_of<c2> = 2;
+// |z|^2 of each lane
+__device__ __forceinline__ float2 abs2(float2 z) { return make_float2(fmaf(z.x, z.x, z.y * z.y), 0.f); }
+__device__ __forceinline__ float2 abs2(c2 z) { return __ffma2_rn(z.re, z.re, __fmul2_rn(z.im, z.im)); }
+// z of lane l
+__device__ __forceinline__ float2 lane(float2 z, int) { return z; }
+__device__ __forceinline__ float2 lane(c2 z, int l) { return l ? make_float2(z.re.y, z.im.y) : make_float2(z.re.x, z.im.x); }
+
 // load v[i R + r] = row[j + r L/R] for this thread's tasks j = lt + i L/16
-template <int L, int R> __device__ __forceinline__ void p2_load(float2 *v, const float2 *row, int lt)
+template <int L, int R, typename E> __device__ __forceinline__ void p2_load(E *v, const E *row, int lt)
 {
     constexpr int TPR = L / 16, T = 16 / R, Q = L / R;
 #pragma unroll
     for (int i = 0; i < T; ++i) {
         const int j = lt + i * TPR;
         if constexpr (Q % 16 == 0) {
-            const float2 *b = row + padi(j);
+            const E *b = row + padi(j);
 #pragma unroll
             for (int r = 0; r < R; ++r) v[i * R + r] = b[r * (Q + Q / 16)];
         } else {
@@ -290,7 +355,7 @@ template <int L, int R> __device__ __forceinline__ void p2_load(float2 *v, const
 }
 
 // Stockham output positions (j / NS) NS R + j mod NS + r NS
-template <int L, int R, int NS> __device__ __forceinline__ void p2_store(const float2 *v, float2 *row, int lt)
+template <int L, int R, int NS, typename E> __device__ __forceinline__ void p2_store(const E *v, E *row, int lt)
 {
     constexpr int TPR = L / 16, T = 16 / R;
 #pragma unroll
@@ -298,11 +363,11 @@ template <int L, int R, int NS> __device__ __forceinline__ void p2_store(const f
         const int j = lt + i * TPR;
         const int idx = (j / NS) * NS * R + (j & (NS - 1));
         if constexpr (NS % 16 == 0) {
-            float2 *b = row + padi(idx);
+            E *b = row + padi(idx);
 #pragma unroll
             for (int r = 0; r < R; ++r) b[r * (NS + NS / 16)] = v[i * R + r];
         } else if constexpr (NS == 1) {
-            float2 *b = row + padi(idx); // idx = R j and (R j mod 16) + r < 16
+            E *b = row + padi(idx); // idx = R j and (R j mod 16) + r < 16
 #pragma unroll
             for (int r = 0; r < R; ++r) b[r] = v[i * R + r];
         } else {
@@ -314,7 +379,7 @@ template <int L, int R, int NS> __device__ __forceinline__ void p2_store(const f
 
 // twiddles exp(2 pi i (j mod NS) r / (NS R)) from a table laid out r-major,
 // tw[r NS + jm], so that consecutive lanes read consecutive words
-template <int R> __device__ __forceinline__ void p2_tw_table(float2 *u, int j, int NS, const float2 *tw)
+template <int R, typename E> __device__ __forceinline__ void p2_tw_table(E *u, int j, int NS, const float2 *tw)
 {
     const float2 *t = tw + (j & (NS - 1));
 #pragma unroll
@@ -322,7 +387,7 @@ template <int R> __device__ __forceinline__ void p2_tw_table(float2 *u, int j, i
 }
 
 // the same by powers of one accurately computed root
-template <int R> __device__ __forceinline__ void p2_tw_pow(float2 *u, int j, int NS)
+template <int R, typename E> __device__ __forceinline__ void p2_tw_pow(E *u, int j, int NS)
 {
     const int jm = j & (NS - 1);
     const float2 w = turn((unsigned)jm, (unsigned)(NS * R));
@@ -334,8 +399,8 @@ template <int R> __device__ __forceinline__ void p2_tw_pow(float2 *u, int j, int
     }
 }
 
-template <int L, int R, int NS, bool TABLE>
-__device__ __forceinline__ void p2_stage(float2 *v, float2 *row, int lt, const float2 *tw)
+template <int L, int R, int NS, bool TABLE, typename E>
+__device__ __forceinline__ void p2_stage(E *v, E *row, int lt, const float2 *tw)
 {
     constexpr int TPR = L / 16, T = 16 / R;
     p2_load<L, R>(v, row, lt);
@@ -348,39 +413,63 @@ __device__ __forceinline__ void p2_stage(float2 *v, float2 *row, int lt, const f
     }
 }
 
-// Rare path of the epilogue (some sample of this thread is above threshold):
-// raise the window maxima.  Kept out of line so that the common path does not
-// carry its registers.
-template <int L, int RL>
-__device__ __noinline__ void p2_triggers(const float2 *v, const FusedArgs &p, int y, int c, int lt, int dlo, int dhi,
-                                         float inv)
+// Rare path of the epilogue: one sample above threshold raises its window's
+// maximum.  Out of line and with scalar arguments, so that the common path
+// keeps every value in registers.
+__device__ __noinline__ void p2_emit(Slot *win, int64_t s, int64_t lo, int64_t window, float r2, float zr, float zi,
+                                     int *err)
 {
-    constexpr int TPR = L / 16, TL = 16 / RL;
+    slot_max(win + (int)((s - lo) / window), make_key(r2, (uint32_t)s), atan2f(zi, zr), err);
+}
+
+// Running maximum of |z|^2 over one lane's outputs d of a row.
+struct Best {
+    float m, zr, zi;
+    int d;
+};
+
+// Visit this thread's outputs d = j + r L/RL in increasing d, so the strict
+// '>' keeps the lowest sample among equal |z|^2.  CHECK limits d to
+// [dlo, dhi) (rows that leave the valid sample range).
+template <int L, int RL, bool CHECK, typename E>
+__device__ __forceinline__ void p2_scan(const E *v, int lt, Best *b, const int *dlo, const int *dhi)
+{
+    constexpr int TPR = L / 16, TL = 16 / RL, NL = lanes_of<E>;
+#pragma unroll
     for (int r = 0; r < RL; ++r)
+#pragma unroll
         for (int i = 0; i < TL; ++i) {
             const int d = lt + i * TPR + r * (L / RL);
-            const float2 z = v[i * RL + r];
-            const float r2 = fmaf(z.x, z.x, z.y * z.y) * inv;
-            if (r2 > p.thr2 && d >= dlo && d < dhi) {
-                const int64_t s = (int64_t)c + (int64_t)p.n1 * d;
-                slot_max(p.win + (size_t)y * p.nwin + (int)((s - p.lo) / p.window), make_key(r2, (uint32_t)s),
-                         atan2f(z.y, z.x), p.err);
+            const float2 m = abs2(v[i * RL + r]);
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                const float ml = l ? m.y : m.x;
+                if (ml > b[l].m && (!CHECK || (d >= dlo[l] && d < dhi[l]))) {
+                    const float2 z = lane(v[i * RL + r], l);
+                    b[l] = {ml, z.x, z.y, d};
+                }
             }
         }
 }
 
-// Grid (n1 / RPC, B).  RPC rows of length L, L/16 threads per row.
-template <int L, int RPC, typename ST, int R0, int R1, int R2, int R3>
+// Grid (rows / RPC, B), rows = n1 (or n1 / 2 row pairs when PAIR).  RPC rows
+// (row pairs) of length L, L/16 threads per row.  In the paired layout lane l
+// of every element belongs to row c + l n1/2, and each packed FP32x2
+// instruction of the transform serves both rows.
+template <int L, int RPC, typename ST, int R0, int R1, int R2, int R3, bool PAIR>
 __global__ void __launch_bounds__(RPC *L / 16) k_pass2(const FusedArgs p)
 {
+    using E = std::conditional_t<PAIR, c2, float2>;
+    constexpr int NL = lanes_of<E>;
     constexpr int TPR = L / 16;
     constexpr int NT = RPC * TPR;
     constexpr int LP = L + L / 16;
     constexpr int NW = NT / 32;
     constexpr int RL = R3 > 1 ? R3 : (R2 > 1 ? R2 : R1);
     constexpr int NSL = L / RL;
-    constexpr int TL = 16 / RL;
-    extern __shared__ float2 sm[];
+    constexpr size_t ROWB = (size_t)L * NL * sizeof(ST); // bytes of one row (pair) of Y
+    extern __shared__ float4 sm4[];
+    E *sm = reinterpret_cast<E *>(sm4);
     __shared__ float2 tw1[R0 * R1]; // stage-1 twiddles (sub-transform size R0)
     __shared__ unsigned long long s_key[NW];
     __shared__ float s_zr[NW], s_zi[NW];
@@ -389,23 +478,31 @@ __global__ void __launch_bounds__(RPC *L / 16) k_pass2(const FusedArgs p)
     const int y = blockIdx.y;
     const int t = p.order[p.base + y];
     const int c = blockIdx.x * RPC + rr;
-    float2 *row = sm + rr * LP;
-    const ST *src = (const ST *)p.ywork + (size_t)y * (size_t)p.n + (size_t)c * L;
+    E *row = sm + rr * LP;
+    const char *yslice = (const char *)p.ywork + (size_t)y * (size_t)p.n * sizeof(ST);
     // tw1[r R0 + jm] = exp(2 pi i jm r / (R0 R1))
     for (int m = tid; m < R0 * R1; m += NT) tw1[m] = turn((m % R0) * (m / R0), R0 * R1);
 
-    float2 v[16];
+    E v[16];
     {
         constexpr int T = 16 / R0;
 #pragma unroll
         for (int i = 0; i < T; ++i) {
             const int j = lt + i * TPR;
 #pragma unroll
-            for (int r = 0; r < R0; ++r) v[i * R0 + r] = ld_c<ST>(src + j + r * (L / R0));
+            for (int r = 0; r < R0; ++r) v[i * R0 + r] = ld_y<ST, PAIR>(yslice, (size_t)c * L + j + r * (L / R0));
             dft<R0, +1>(v + i * R0);
         }
         p2_store<L, R0, 1>(v, row, lt);
         __syncthreads();
+    }
+    {
+        // Y is read exactly once: invalidate its L2 lines so that, when a batch
+        // stays resident in L2 between the passes, they are never written back
+        constexpr int LINES = (int)(RPC * ROWB / 128);
+        const char *yb = yslice + (size_t)blockIdx.x * RPC * ROWB;
+        for (int m = tid; m < LINES; m += NT)
+            asm volatile("discard.global.L2 [%0], 128;" ::"l"(yb + (size_t)m * 128) : "memory");
     }
     if constexpr (R2 > 1) {
         p2_stage<L, R1, R0, true>(v, row, lt, tw1);
@@ -421,49 +518,78 @@ __global__ void __launch_bounds__(RPC *L / 16) k_pass2(const FusedArgs p)
     }
     p2_stage<L, RL, NSL, R2 == 1>(v, row, lt, tw1);
 
-    // Epilogue.  Output d = j + r L/RL of this row is sample s = c + n1 d; in
-    // (r, i) order d increases, so the strict '>' keeps the lowest sample
-    // among equal |z|^2.  |z|^2 is compared before the (positive) scaling.
+    // Epilogue.  Output d of lane l is sample s = c_l + n1 d with
+    // c_l = c + l n1/2; |z|^2 is compared before the (positive) scaling.
     const float inv = p.invnorm[t];
     const int n1 = p.n1;
     const int64_t lo = p.lo, hi = p.hi;
-    int dlo = 0, dhi = L;
-    if (!(lo <= c && (int64_t)c + (int64_t)n1 * (L - 1) < hi)) {
-        dlo = (int)max((int64_t)0, (lo - c + n1 - 1) / n1);
-        dhi = (int)min((int64_t)L, hi > c ? (hi - c + n1 - 1) / n1 : (int64_t)0);
-    }
-    float best = -1.f, bzr = 0.f, bzi = 0.f;
-    int bd = 0;
+    int64_t cl[NL];
+    int dlo[NL], dhi[NL];
+    bool full = true;
+    Best b[NL];
 #pragma unroll
-    for (int r = 0; r < RL; ++r)
-#pragma unroll
-        for (int i = 0; i < TL; ++i) {
-            const int d = lt + i * TPR + r * (L / RL);
-            const float2 z = v[i * RL + r];
-            const float m = fmaf(z.x, z.x, z.y * z.y);
-            if (m > best && d >= dlo && d < dhi) {
-                best = m;
-                bd = d;
-                bzr = z.x;
-                bzi = z.y;
-            }
+    for (int l = 0; l < NL; ++l) {
+        cl[l] = c + (int64_t)l * (n1 / 2);
+        dlo[l] = 0;
+        dhi[l] = L;
+        if (!(lo <= cl[l] && cl[l] + (int64_t)n1 * (L - 1) < hi)) {
+            full = false;
+            dlo[l] = (int)max((int64_t)0, (lo - cl[l] + n1 - 1) / n1);
+            dhi[l] = (int)min((int64_t)L, hi > cl[l] ? (hi - cl[l] + n1 - 1) / n1 : (int64_t)0);
         }
-    if (best * inv > p.thr2) p2_triggers<L, RL>(v, p, y, c, lt, dlo, dhi, inv);
-    unsigned long long key = best >= 0.f ? make_key(best * inv, (uint32_t)(c + n1 * bd)) : 0ull;
+        b[l] = {-1.f, 0.f, 0.f, 0};
+    }
+    if (full) p2_scan<L, RL, false>(v, lt, b, dlo, dhi);
+    else p2_scan<L, RL, true>(v, lt, b, dlo, dhi);
+
+    float mx = b[0].m;
+#pragma unroll
+    for (int l = 1; l < NL; ++l) mx = fmaxf(mx, b[l].m);
+    if (mx * inv > p.thr2) {
+        constexpr int TL = 16 / RL;
+        Slot *win = p.win + (size_t)y * p.nwin;
+#pragma unroll
+        for (int r = 0; r < RL; ++r)
+#pragma unroll
+            for (int i = 0; i < TL; ++i) {
+                const int d = lt + i * TPR + r * (L / RL);
+                const float2 m = abs2(v[i * RL + r]);
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    const float r2 = (l ? m.y : m.x) * inv;
+                    if (r2 > p.thr2 && d >= dlo[l] && d < dhi[l]) {
+                        const float2 z = lane(v[i * RL + r], l);
+                        p2_emit(win, cl[l] + (int64_t)n1 * d, lo, p.window, r2, z.x, z.y, p.err);
+                    }
+                }
+            }
+    }
+    unsigned long long key = 0ull;
+    float bzr = 0.f, bzi = 0.f;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const unsigned long long k =
+            b[l].m >= 0.f ? make_key(b[l].m * inv, (uint32_t)(cl[l] + (int64_t)n1 * b[l].d)) : 0ull;
+        if (k > key) {
+            key = k;
+            bzr = b[l].zr;
+            bzi = b[l].zi;
+        }
+    }
     warp_max_key(key, bzr, bzi);
-    const int lane = tid & 31, wid = tid >> 5;
-    if (lane == 0) {
+    const int lane_id = tid & 31, wid = tid >> 5;
+    if (lane_id == 0) {
         s_key[wid] = key;
         s_zr[wid] = bzr;
         s_zi[wid] = bzi;
     }
     __syncthreads();
     if (wid == 0) {
-        key = lane < NW ? s_key[lane] : 0ull;
-        bzr = lane < NW ? s_zr[lane] : 0.f;
-        bzi = lane < NW ? s_zi[lane] : 0.f;
+        key = lane_id < NW ? s_key[lane_id] : 0ull;
+        bzr = lane_id < NW ? s_zr[lane_id] : 0.f;
+        bzi = lane_id < NW ? s_zi[lane_id] : 0.f;
         warp_max_key(key, bzr, bzi);
-        if (lane == 0 && key != 0ull) slot_max(p.peak + t, key, atan2f(bzi, bzr), p.err);
+        if (lane_id == 0 && key != 0ull) slot_max(p.peak + t, key, atan2f(bzi, bzr), p.err);
     }
 }
 
@@ -474,10 +600,16 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-constexpr int kPass1Group = 4; // templates per pass-1 CTA
+constexpr int kPass1Group = 4;    // templates per pass-1 CTA
+constexpr int kPairMaxL = 8192;   // pass 2 runs on row pairs up to this row length
+
+static bool paired(int n2) { return n2 <= kPairMaxL; }
 
 size_t fused_pass1_smem(int n1, int ccols) { return (size_t)n1 * ccols * sizeof(float2); }
-size_t fused_pass2_smem(int n2, int rpc) { return (size_t)rpc * (n2 + n2 / 16) * sizeof(float2); }
+size_t fused_pass2_smem(int n2, int rpc)
+{
+    return (size_t)rpc * (n2 + n2 / 16) * (paired(n2) ? sizeof(c2) : sizeof(float2));
+}
 
 bool fused_supported(int log2n) { return log2n >= 12 && log2n <= 22; }
 
@@ -498,7 +630,7 @@ void fused_default_tiling(int log2n, int *n1, int *ccols, int *rpc)
 {
     static const int tab[23][2] = {{0, 0},  {0, 0},  {0, 0},  {0, 0},  {0, 0},  {0, 0},  {0, 0},  {0, 0},
                                    {0, 0},  {0, 0},  {0, 0},  {0, 0},  {64, 32}, {64, 16}, {64, 8}, {64, 4},
-                                   {64, 4}, {128, 4}, {256, 4}, {256, 2}, {256, 2}, {256, 1}, {256, 1}};
+                                   {64, 4}, {128, 4}, {256, 4}, {256, 2}, {256, 1}, {256, 1}, {256, 1}};
     *n1 = tab[log2n][0];
     *rpc = tab[log2n][1];
     *ccols = 32;
@@ -507,7 +639,7 @@ void fused_default_tiling(int log2n, int *n1, int *ccols, int *rpc)
 template <int N1, int R0, int R1, int C, typename ST>
 static cudaError_t run_pass1(const FusedArgs &a, int count, cudaStream_t s)
 {
-    auto k = k_pass1<N1, R0, R1, C, kPass1Group, ST>;
+    auto k = paired(a.n2) ? k_pass1<N1, R0, R1, C, kPass1Group, ST, true> : k_pass1<N1, R0, R1, C, kPass1Group, ST, false>;
     const size_t smem = fused_pass1_smem(N1, C);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
@@ -533,11 +665,12 @@ template <typename ST> static cudaError_t pass1_dispatch(const FusedArgs &a, int
 template <int L, int RPC, typename ST, int R0, int R1, int R2, int R3>
 static cudaError_t run_pass2(const FusedArgs &a, int count, cudaStream_t s)
 {
-    auto k = k_pass2<L, RPC, ST, R0, R1, R2, R3>;
+    constexpr bool PAIR = L <= kPairMaxL;
+    auto k = k_pass2<L, RPC, ST, R0, R1, R2, R3, PAIR>;
     const size_t smem = fused_pass2_smem(L, RPC);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)(a.n1 / RPC), (unsigned)count);
+    dim3 grid((unsigned)(a.n1 / (PAIR ? 2 : 1) / RPC), (unsigned)count);
     k<<<grid, RPC * L / 16, smem, s>>>(a);
     return cudaGetLastError();
 }
