@@ -164,7 +164,7 @@ cui_status cui_bank_template(cui_bank bank, int64_t t, float *out_dev);
  * batch * N complex values, live in a workspace between the passes). */
 typedef struct {
     int32_t n1;    /* 64, 128 or 256 (subject to the kernels built for N) */
-    int32_t ccols; /* 32 or 64 */
+    int32_t ccols; /* 16, 32 or 64 */
     int32_t rpc;   /* rows per pass-2 CTA */
     int32_t batch; /* templates per launch pair, >= 1 */
 } cui_tuning;

@@ -760,7 +760,7 @@ extern "C" cui_status cui_bank_autotune(cui_bank b, int32_t reps, cui_tuning *be
     CUI_TRY(cudaEventCreate(&e1), "autotune events");
     cui_tuning cur = {b->n1, b->ccols, b->rpc, b->batch}, top = cur;
     double top_ms = 1e300;
-    const int n1s[] = {64, 128, 256}, ccs[] = {32, 64}, rpcs[] = {1, 2, 4, 8, 16, 32};
+    const int n1s[] = {64, 128, 256}, ccs[] = {16, 32, 64}, rpcs[] = {1, 2, 4, 8, 16, 32};
     const int64_t per = b->n * ((b->desc.flags & CUI_STORE_BF16) ? 4 : 8);
     std::vector<int> batches;
     for (int64_t bt = 16; bt <= 4096; bt *= 4)

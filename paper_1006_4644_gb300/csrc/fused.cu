@@ -224,15 +224,17 @@ __device__ __forceinline__ void p1_stage0(float2 *v, const FusedArgs &p, const f
 // position (the stage-1 table and the inter-pass factors exp(2 pi i b c / N),
 // kept in registers) are computed once per CTA.  PAIR selects the paired
 // layout of Y (rows c and c + n1/2 interleaved), else rows are stored whole.
+constexpr int p1_min_blocks(int nt) { return nt == 256 ? 3 : (nt <= 512 ? 2 : 1); }
+
 template <int N1, int R0, int R1, int C, int G, typename ST, bool PAIR>
-__global__ void __launch_bounds__(C *N1 / 16, (C * N1 / 16 <= 512 ? 2 : 1)) k_pass1(const FusedArgs p, int count)
+__global__ void __launch_bounds__(C *N1 / 16, p1_min_blocks(C *N1 / 16)) k_pass1(const FusedArgs p, int count)
 {
     constexpr int NT = C * N1 / 16;
     constexpr int NROW = N1 / 2;
     constexpr int T1 = 16 / R1;
-    __shared__ float4 anc[NROW];
+    __shared__ float4 anc[G][NROW];
     __shared__ float2 tw[N1];
-    __shared__ float2 cdf[kNB];
+    __shared__ float2 cdf[G][kNB];
     extern __shared__ float2 sm[]; // [N1][C]
     const int tid = threadIdx.x;
     const int col = tid % C;
@@ -253,29 +255,39 @@ __global__ void __launch_bounds__(C *N1 / 16, (C * N1 / 16 <= 512 ? 2 : 1)) k_pa
         ipb[i] = turn(((unsigned)bcol * (unsigned)(jt + i * (N1 / 16))) & (unsigned)(N - 1), (unsigned)N);
     const float2 ips = turn(((unsigned)bcol * (unsigned)(N1 / R1)) & (unsigned)(N - 1), (unsigned)N);
 
-    for (int g = 0; g < G; ++g) {
-        const int y = blockIdx.y * G + g;
-        if (y >= count) break;
+    // anchors of all the CTA's templates in one balanced phase
+    const int y0 = blockIdx.y * G;
+    const int ng = min(G, count - y0);
+    const int a_lo = ceil_div_pos(klo - b0 - (C - 1), n2);
+    for (int m = tid; m < G * NROW; m += NT) {
+        const int g = m / NROW, a = m % NROW;
+        if (g >= ng || a < a_lo) continue;
+        const int t = p.order[p.base + y0 + g];
+        if (a < min(NROW, ceil_div_pos(p.khi[t] - b0, n2))) {
+            const int64_t ai = (int64_t)a * (n2 / C) + cb;
+            anc[g][a] = anchor_eval(p, t, ai, (float)((int64_t)n2 * a + b0 + C / 2));
+        }
+    }
+    if (tid < G * kNB && tid / kNB < ng)
+        cdf[tid / kNB][tid % kNB] = p.coef_df[(int64_t)p.order[p.base + y0 + tid / kNB] * kNB + tid % kNB];
+    __syncthreads();
+
+    for (int g = 0; g < ng; ++g) {
+        const int y = y0 + g;
         const int t = p.order[p.base + y];
         const int khi = p.khi[t];
         const int kex = p.kex[t];
-        const int a_lo = ceil_div_pos(klo - b0 - (C - 1), n2);
         const int a_hi = min(NROW, ceil_div_pos(khi - b0, n2));
-        if (tid < kNB) cdf[tid] = p.coef_df[(int64_t)t * kNB + tid];
-        for (int a = a_lo + tid; a < a_hi; a += NT) {
-            const int64_t ai = (int64_t)a * (n2 / C) + cb;
-            anc[a] = anchor_eval(p, t, ai, (float)((int64_t)n2 * a + b0 + C / 2));
-        }
-        __syncthreads();
 
         float2 v[16];
         // number of stage-0 inputs per task that can be nonzero, rounded up to a power of two
         const int nzr = ceil_div_pos(a_hi, N1 / R0);
-        if (nzr <= 1) p1_stage0<N1, R0, C, 1>(v, p, anc, cdf, jt, col, b0, a_lo, a_hi, klo, khi, kex);
-        else if (nzr <= 2) p1_stage0<N1, R0, C, 2>(v, p, anc, cdf, jt, col, b0, a_lo, a_hi, klo, khi, kex);
-        else if (nzr <= 4 || R0 <= 8) p1_stage0<N1, R0, C, (R0 > 8 ? 4 : R0 / 2)>(v, p, anc, cdf, jt, col, b0, a_lo,
-                                                                                    a_hi, klo, khi, kex);
-        else p1_stage0<N1, R0, C, R0 / 2>(v, p, anc, cdf, jt, col, b0, a_lo, a_hi, klo, khi, kex);
+        if (nzr <= 1) p1_stage0<N1, R0, C, 1>(v, p, anc[g], cdf[g], jt, col, b0, a_lo, a_hi, klo, khi, kex);
+        else if (nzr <= 2) p1_stage0<N1, R0, C, 2>(v, p, anc[g], cdf[g], jt, col, b0, a_lo, a_hi, klo, khi, kex);
+        else if (nzr <= 4 || R0 <= 8) p1_stage0<N1, R0, C, (R0 > 8 ? 4 : R0 / 2)>(v, p, anc[g], cdf[g], jt, col, b0,
+                                                                                    a_lo, a_hi, klo, khi, kex);
+        else p1_stage0<N1, R0, C, R0 / 2>(v, p, anc[g], cdf[g], jt, col, b0, a_lo, a_hi, klo, khi, kex);
+        if (g > 0) __syncthreads(); // every thread has read the previous template's sm
 #pragma unroll
         for (int i = 0; i < 16 / R0; ++i) {
             const int j = jt + i * (N1 / 16);
@@ -616,7 +628,7 @@ bool fused_supported(int log2n) { return log2n >= 12 && log2n <= 22; }
 // A tiling has kernels when pass 1 exists for (n1, ccols) and pass 2 for (n2, rpc).
 bool fused_tiling_ok(int log2n, int n1, int ccols, int rpc)
 {
-    if (!fused_supported(log2n) || (n1 != 64 && n1 != 128 && n1 != 256) || (ccols != 32 && ccols != 64)) return false;
+    if (!fused_supported(log2n) || (n1 != 64 && n1 != 128 && n1 != 256) || (ccols != 16 && ccols != 32 && ccols != 64)) return false;
     const int64_t n2 = (int64_t(1) << log2n) / n1;
     if (n2 % ccols) return false;
     static const int pass2[][2] = {{64, 32},  {128, 16}, {256, 8},  {512, 4},  {1024, 4},
@@ -650,7 +662,11 @@ static cudaError_t run_pass1(const FusedArgs &a, int count, cudaStream_t s)
 
 template <typename ST> static cudaError_t pass1_dispatch(const FusedArgs &a, int count, cudaStream_t s)
 {
-    if (a.ccols == 32) {
+    if (a.ccols == 16) {
+        if (a.n1 == 64) return run_pass1<64, 8, 8, 16, ST>(a, count, s);
+        if (a.n1 == 128) return run_pass1<128, 8, 16, 16, ST>(a, count, s);
+        if (a.n1 == 256) return run_pass1<256, 16, 16, 16, ST>(a, count, s);
+    } else if (a.ccols == 32) {
         if (a.n1 == 64) return run_pass1<64, 8, 8, 32, ST>(a, count, s);
         if (a.n1 == 128) return run_pass1<128, 8, 16, 32, ST>(a, count, s);
         if (a.n1 == 256) return run_pass1<256, 16, 16, 32, ST>(a, count, s);

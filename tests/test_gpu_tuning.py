@@ -23,7 +23,7 @@ def _tilings(bank, n):
     from paper_1006_4644_gb300 import CuiError
 
     out = []
-    for n1, cc, rpc in itertools.product([64, 128, 256], [32, 64], [1, 2, 4, 8, 16, 32]):
+    for n1, cc, rpc in itertools.product([64, 128, 256], [16, 32, 64], [1, 2, 4, 8, 16, 32]):
         try:
             bank.set_tuning(n1, cc, rpc, 3)
             out.append((n1, cc, rpc))
