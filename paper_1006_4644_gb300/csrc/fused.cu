@@ -348,10 +348,10 @@ __device__ __forceinline__ float2 abs2(c2 z) { return __ffma2_rn(z.re, z.re, __f
 __device__ __forceinline__ float2 lane(float2 z, int) { return z; }
 __device__ __forceinline__ float2 lane(c2 z, int l) { return l ? make_float2(z.re.y, z.im.y) : make_float2(z.re.x, z.im.x); }
 
-// load v[i R + r] = row[j + r L/R] for this thread's tasks j = lt + i L/16
-template <int L, int R, typename E> __device__ __forceinline__ void p2_load(E *v, const E *row, int lt)
+// load v[i R + r] = row[j + r L/R] for this thread's tasks j = lt + i L/PPT
+template <int L, int R, int PPT, typename E> __device__ __forceinline__ void p2_load(E *v, const E *row, int lt)
 {
-    constexpr int TPR = L / 16, T = 16 / R, Q = L / R;
+    constexpr int TPR = L / PPT, T = PPT / R, Q = L / R;
 #pragma unroll
     for (int i = 0; i < T; ++i) {
         const int j = lt + i * TPR;
@@ -367,9 +367,10 @@ template <int L, int R, typename E> __device__ __forceinline__ void p2_load(E *v
 }
 
 // Stockham output positions (j / NS) NS R + j mod NS + r NS
-template <int L, int R, int NS, typename E> __device__ __forceinline__ void p2_store(const E *v, E *row, int lt)
+template <int L, int R, int NS, int PPT, typename E>
+__device__ __forceinline__ void p2_store(const E *v, E *row, int lt)
 {
-    constexpr int TPR = L / 16, T = 16 / R;
+    constexpr int TPR = L / PPT, T = PPT / R;
 #pragma unroll
     for (int i = 0; i < T; ++i) {
         const int j = lt + i * TPR;
@@ -411,11 +412,11 @@ template <int R, typename E> __device__ __forceinline__ void p2_tw_pow(E *u, int
     }
 }
 
-template <int L, int R, int NS, bool TABLE, typename E>
+template <int L, int R, int NS, bool TABLE, int PPT, typename E>
 __device__ __forceinline__ void p2_stage(E *v, E *row, int lt, const float2 *tw)
 {
-    constexpr int TPR = L / 16, T = 16 / R;
-    p2_load<L, R>(v, row, lt);
+    constexpr int TPR = L / PPT, T = PPT / R;
+    p2_load<L, R, PPT>(v, row, lt);
 #pragma unroll
     for (int i = 0; i < T; ++i) {
         const int j = lt + i * TPR;
@@ -443,10 +444,10 @@ struct Best {
 // Visit this thread's outputs d = j + r L/RL in increasing d, so the strict
 // '>' keeps the lowest sample among equal |z|^2.  CHECK limits d to
 // [dlo, dhi) (rows that leave the valid sample range).
-template <int L, int RL, bool CHECK, typename E>
+template <int L, int RL, bool CHECK, int PPT, typename E>
 __device__ __forceinline__ void p2_scan(const E *v, int lt, Best *b, const int *dlo, const int *dhi)
 {
-    constexpr int TPR = L / 16, TL = 16 / RL, NL = lanes_of<E>;
+    constexpr int TPR = L / PPT, TL = PPT / RL, NL = lanes_of<E>;
 #pragma unroll
     for (int r = 0; r < RL; ++r)
 #pragma unroll
@@ -465,15 +466,15 @@ __device__ __forceinline__ void p2_scan(const E *v, int lt, Best *b, const int *
 }
 
 // Grid (rows / RPC, B), rows = n1 (or n1 / 2 row pairs when PAIR).  RPC rows
-// (row pairs) of length L, L/16 threads per row.  In the paired layout lane l
+// (row pairs) of length L, L/PPT threads per row, PPT points per thread.  In the paired layout lane l
 // of every element belongs to row c + l n1/2, and each packed FP32x2
 // instruction of the transform serves both rows.
-template <int L, int RPC, typename ST, int R0, int R1, int R2, int R3, bool PAIR>
-__global__ void __launch_bounds__(RPC *L / 16) k_pass2(const FusedArgs p)
+template <int L, int RPC, typename ST, int R0, int R1, int R2, int R3, bool PAIR, int PPT>
+__global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
 {
     using E = std::conditional_t<PAIR, c2, float2>;
     constexpr int NL = lanes_of<E>;
-    constexpr int TPR = L / 16;
+    constexpr int TPR = L / PPT;
     constexpr int NT = RPC * TPR;
     constexpr int LP = L + L / 16;
     constexpr int NW = NT / 32;
@@ -483,6 +484,7 @@ __global__ void __launch_bounds__(RPC *L / 16) k_pass2(const FusedArgs p)
     extern __shared__ float4 sm4[];
     E *sm = reinterpret_cast<E *>(sm4);
     __shared__ float2 tw1[R0 * R1]; // stage-1 twiddles (sub-transform size R0)
+    __shared__ float2 tw2[R3 > 1 ? R0 * R1 * R2 : 1]; // stage-2 twiddles of four-stage rows
     __shared__ unsigned long long s_key[NW];
     __shared__ float s_zr[NW], s_zi[NW];
     const int tid = threadIdx.x;
@@ -494,10 +496,13 @@ __global__ void __launch_bounds__(RPC *L / 16) k_pass2(const FusedArgs p)
     const char *yslice = (const char *)p.ywork + (size_t)y * (size_t)p.n * sizeof(ST);
     // tw1[r R0 + jm] = exp(2 pi i jm r / (R0 R1))
     for (int m = tid; m < R0 * R1; m += NT) tw1[m] = turn((m % R0) * (m / R0), R0 * R1);
+    if constexpr (R3 > 1)
+        for (int m = tid; m < R0 * R1 * R2; m += NT)
+            tw2[m] = turn((m % (R0 * R1)) * (m / (R0 * R1)), R0 * R1 * R2);
 
-    E v[16];
+    E v[PPT];
     {
-        constexpr int T = 16 / R0;
+        constexpr int T = PPT / R0;
 #pragma unroll
         for (int i = 0; i < T; ++i) {
             const int j = lt + i * TPR;
@@ -505,7 +510,7 @@ __global__ void __launch_bounds__(RPC *L / 16) k_pass2(const FusedArgs p)
             for (int r = 0; r < R0; ++r) v[i * R0 + r] = ld_y<ST, PAIR>(yslice, (size_t)c * L + j + r * (L / R0));
             dft<R0, +1>(v + i * R0);
         }
-        p2_store<L, R0, 1>(v, row, lt);
+        p2_store<L, R0, 1, PPT>(v, row, lt);
         __syncthreads();
     }
     {
@@ -517,18 +522,18 @@ __global__ void __launch_bounds__(RPC *L / 16) k_pass2(const FusedArgs p)
             asm volatile("discard.global.L2 [%0], 128;" ::"l"(yb + (size_t)m * 128) : "memory");
     }
     if constexpr (R2 > 1) {
-        p2_stage<L, R1, R0, true>(v, row, lt, tw1);
+        p2_stage<L, R1, R0, true, PPT>(v, row, lt, tw1);
         __syncthreads();
-        p2_store<L, R1, R0>(v, row, lt);
+        p2_store<L, R1, R0, PPT>(v, row, lt);
         __syncthreads();
         if constexpr (R3 > 1) {
-            p2_stage<L, R2, R0 * R1, false>(v, row, lt, tw1);
+            p2_stage<L, R2, R0 * R1, true, PPT>(v, row, lt, tw2);
             __syncthreads();
-            p2_store<L, R2, R0 * R1>(v, row, lt);
+            p2_store<L, R2, R0 * R1, PPT>(v, row, lt);
             __syncthreads();
         }
     }
-    p2_stage<L, RL, NSL, R2 == 1>(v, row, lt, tw1);
+    p2_stage<L, RL, NSL, R2 == 1, PPT>(v, row, lt, tw1);
 
     // Epilogue.  Output d of lane l is sample s = c_l + n1 d with
     // c_l = c + l n1/2; |z|^2 is compared before the (positive) scaling.
@@ -551,14 +556,14 @@ __global__ void __launch_bounds__(RPC *L / 16) k_pass2(const FusedArgs p)
         }
         b[l] = {-1.f, 0.f, 0.f, 0};
     }
-    if (full) p2_scan<L, RL, false>(v, lt, b, dlo, dhi);
-    else p2_scan<L, RL, true>(v, lt, b, dlo, dhi);
+    if (full) p2_scan<L, RL, false, PPT>(v, lt, b, dlo, dhi);
+    else p2_scan<L, RL, true, PPT>(v, lt, b, dlo, dhi);
 
     float mx = b[0].m;
 #pragma unroll
     for (int l = 1; l < NL; ++l) mx = fmaxf(mx, b[l].m);
     if (mx * inv > p.thr2) {
-        constexpr int TL = 16 / RL;
+        constexpr int TL = PPT / RL;
         Slot *win = p.win + (size_t)y * p.nwin;
 #pragma unroll
         for (int r = 0; r < RL; ++r)
@@ -678,16 +683,16 @@ template <typename ST> static cudaError_t pass1_dispatch(const FusedArgs &a, int
     return cudaErrorInvalidValue;
 }
 
-template <int L, int RPC, typename ST, int R0, int R1, int R2, int R3>
+template <int L, int RPC, typename ST, int R0, int R1, int R2, int R3, int PPT = 16>
 static cudaError_t run_pass2(const FusedArgs &a, int count, cudaStream_t s)
 {
     constexpr bool PAIR = L <= kPairMaxL;
-    auto k = k_pass2<L, RPC, ST, R0, R1, R2, R3, PAIR>;
+    auto k = k_pass2<L, RPC, ST, R0, R1, R2, R3, PAIR, PPT>;
     const size_t smem = fused_pass2_smem(L, RPC);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(a.n1 / (PAIR ? 2 : 1) / RPC), (unsigned)count);
-    k<<<grid, RPC * L / 16, smem, s>>>(a);
+    k<<<grid, RPC * L / PPT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
