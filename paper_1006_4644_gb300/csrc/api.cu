@@ -282,7 +282,7 @@ static void release(cui_bank b)
 {
     void *ptrs[] = {b->d_coef, b->d_coef_df, b->d_mass, b->d_khi, b->d_sigma2, b->d_invnorm, b->d_peak, b->d_peaks,
                     b->d_iota, b->d_strain, b->d_psd, b->d_amp, b->d_prefix, b->d_scan, b->d_fa, b->d_fb,
-                    b->tw.lo64, b->tw.hi64, b->tw.lo32, b->tw.hi32,
+                    b->tw.lo64, b->tw.hi64, b->tw.lo32, b->tw.hi32, b->tw.lodf, b->tw.hidf,
                     b->d_wbar, b->d_dS, b->d_scales, b->d_basis, b->d_basis_df, b->d_kex, b->d_gexact, b->d_y,
                     b->d_win, b->d_h, b->d_qa, b->d_qb, b->d_acc, b->d_pwin, b->d_trig, b->d_trig_count, b->d_err,
                     b->d_order};
@@ -455,6 +455,8 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     chk(dalloc(&b->tw.hi64, int64_t(1) << (b->log2n - b->tw.shift)));
     chk(dalloc(&b->tw.lo32, int64_t(1) << b->tw.shift));
     chk(dalloc(&b->tw.hi32, int64_t(1) << (b->log2n - b->tw.shift)));
+    chk(dalloc(&b->tw.lodf, int64_t(1) << b->tw.shift));
+    chk(dalloc(&b->tw.hidf, int64_t(1) << (b->log2n - b->tw.shift)));
     chk(dalloc(&b->d_trig, b->trig_cap));
     chk(dalloc(&b->d_trig_count, 1));
     chk(dalloc(&b->d_err, 1));
@@ -533,9 +535,8 @@ extern "C" cui_status cui_segment_upload(cui_bank b, const double *strain, int64
     CUI_TRY(cudaMemcpyAsync(b->d_strain, strain, sizeof(double) * b->n, kind, s), "strain copy");
     CUI_TRY(cudaMemcpyAsync(b->d_psd, psd, sizeof(double) * (b->nh + 1), kind, s), "psd copy");
     Span span(b, 0);
-    launch_real_to_complex(b->d_strain, b->d_fa, b->n, s);
     double2 *X = nullptr;
-    launch_fft_passes_f64(b->d_fa, b->d_fb, b->log2n, -1, b->tw, s, &X);
+    launch_segment_transform_df(b->d_strain, b->d_fa, b->d_fb, b->log2n, b->tw, s, &X);
     b->d_X = X;
     launch_weighted_data(X, b->d_psd, b->d_amp, b->n, b->k_low, b->desc.sample_rate, b->d_scales, b->d_wbar,
                          b->d_dS, b->plain_fp64, s);

@@ -300,6 +300,36 @@ __device__ __forceinline__ df df_mul(df a, df b)
     return quick_two_sum(p, e);
 }
 
+// Transform arithmetic on double-float values: the sum keeps the exact
+// two-sum of the high parts and adds the low parts once (error ~2^-47 of the
+// larger operand, which is what a transform's error is measured against).
+// With these operators and `dfc`, the generic DFTs above run in double-float.
+__device__ __forceinline__ df operator+(df a, df b)
+{
+    const df s = two_sum(a.hi, b.hi);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) { return df_mul(a, b); }
+__device__ __forceinline__ df operator*(int sign, df a) { return sign > 0 ? a : -a; }
+
+struct dfc {
+    df x, y;
+};
+template <> struct cpx<df> { using T = dfc; };
+__device__ __forceinline__ dfc mk(df x, df y) { return {x, y}; }
+__device__ __forceinline__ dfc operator+(dfc a, dfc b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ dfc operator-(dfc a, dfc b) { return {a.x - b.x, a.y - b.y}; }
+
+// the radix-16 constants split into high and low floats
+constexpr df df_const(double v) { return {(float)v, (float)(v - (double)(float)v)}; }
+template <> struct k16<df> {
+    static constexpr df c1 = df_const(0.92387953251128675613); // cos(pi/8)
+    static constexpr df s1 = df_const(0.38268343236508977173); // sin(pi/8)
+    static constexpr df r2 = df_const(0.70710678118654752440); // cos(pi/4)
+};
+
 // ------------------------------------------------------ best-sample slot ---
 // 16 bytes: key = (float bits of rho^2) << 32 | (0xFFFFFFFF - sample), so the
 // largest key is the largest rho^2 and, among equal rho^2, the lowest sample;

@@ -43,6 +43,7 @@ struct Twiddles {
     double2 *lo64, *hi64;
     float2 *lo32, *hi32;
     int shift, log2n;
+    dfc *lodf = nullptr, *hidf = nullptr; // the same in double-float, when allocated
 };
 void launch_twiddle_tables(const Twiddles &t, cudaStream_t s);
 void launch_fft_passes_f64(double2 *a, double2 *b, int log2n, int sign, const Twiddles &tw, cudaStream_t s,
@@ -50,7 +51,10 @@ void launch_fft_passes_f64(double2 *a, double2 *b, int log2n, int sign, const Tw
 // batch transforms of length 2^log2n stored back to back (grid rows)
 void launch_fft_passes_f32(float2 *a, float2 *b, int log2n, int sign, const Twiddles &tw, cudaStream_t s,
                            float2 **result, int batch = 1);
-void launch_real_to_complex(const double *d, double2 *out, int64_t n, cudaStream_t s);
+// d~ = DFT(d) (sign -1) of a real series in double-float arithmetic, returned
+// as FP64 complex bins 0 .. N/2 in one of the two N-element buffers (a or b)
+void launch_segment_transform_df(const double *d, double2 *a, double2 *b, int log2n, const Twiddles &tw,
+                                 cudaStream_t s, double2 **result);
 void launch_amp_table(double *amp, int64_t nhalf, cudaStream_t s);
 void launch_weighted_data(const double2 *X, const double *psd, const double *amp, int64_t n, int k_low,
                           double fs, SegScales *scales, float2 *wbar, void *dS, bool dS_fp64, cudaStream_t s);

@@ -76,15 +76,15 @@ static void stage(const cpx_t<Rl> *in, cpx_t<Rl> *out, int64_t L, int64_t Ns, in
 // multiple of 4) then radix-16 stages, ping-ponging between a and b.
 template <typename Rl>
 static void fft_passes(cpx_t<Rl> *a, cpx_t<Rl> *b, int log2n, int sign, const TwTab<Rl> &tw, cudaStream_t s,
-                       cpx_t<Rl> **result, int batch = 1)
+                       cpx_t<Rl> **result, int batch = 1, int max_lr = 4)
 {
     const int64_t L = int64_t(1) << log2n;
     int64_t Ns = 1;
     cpx_t<Rl> *src = a, *dst = b;
-    int rem = log2n % 4;
+    int rem = log2n % max_lr;
     int left = log2n;
     while (left > 0) {
-        int lr = rem ? rem : 4;
+        int lr = rem ? rem : max_lr;
         rem = 0;
         int R = 1 << lr;
         if (sign > 0) stage<Rl, +1>(src, dst, L, Ns, R, tw, s, batch);
@@ -109,6 +109,61 @@ void launch_fft_passes_f32(float2 *a, float2 *b, int log2n, int sign, const Twid
     fft_passes<float>(a, b, log2n, sign, TwTab<float>{tw.lo32, tw.hi32, tw.shift, tw.log2n}, s, result, batch);
 }
 
+// Segment transform in double-float.  FP64 runs at a small fraction of the
+// FP32 rate on this GPU, while a double-float value (hi + lo, 48 significant
+// bits) costs a handful of FP32 operations, so the once-per-segment transform
+// keeps near-FP64 accuracy at FP32 speed.  The input is scaled by 2^kDfShift
+// (exact) so that strain of ~1e-21 and its spectrum sit far from the FP32
+// range limits; the output is scaled back.
+constexpr int kDfShift = 64;
+// radix of the double-float passes: small radices give the long double-float
+// dependency chains enough threads to hide their latency
+constexpr int kDfLog2Radix = 4;
+
+// x 2^kDfShift as hi + lo from the bits of x alone (integer and FP32 operations;
+// FP64 arithmetic is the slow path on this GPU): hi carries the top 24
+// significant bits (truncated), lo the remaining 29 rounded to 24.  Zero and
+// subnormal inputs give zero.
+__device__ __forceinline__ df split_double(double x)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((u >> 52) & 0x7FF);
+    if (e == 0) return {0.f, 0.f};
+    const unsigned sign = (unsigned)(u >> 63) << 31;
+    const float hi1 = __uint_as_float(sign | (127u << 23) | (unsigned)((u >> 29) & 0x7FFFFF)); // +-1.m
+    const float lo1 = __uint_as_float(__float_as_uint((float)(unsigned)(u & 0x1FFFFFFF)) | sign);
+    return {ldexpf(hi1, e - 1023 + kDfShift), ldexpf(lo1, e - 1075 + kDfShift)};
+}
+
+__global__ void k_real_to_dfc(const double *__restrict__ d, dfc *__restrict__ out, int64_t n)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        out[j] = dfc{split_double(d[j]), df{0.f, 0.f}};
+}
+
+// bins 0 .. n-1 back to FP64 in place (only the one-sided half is read later)
+__global__ void k_dfc_to_double(dfc *io, int64_t n)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const dfc v = io[j];
+        reinterpret_cast<double2 *>(io)[j] = make_double2(ldexp((double)v.x.hi + (double)v.x.lo, -kDfShift),
+                                                          ldexp((double)v.y.hi + (double)v.y.lo, -kDfShift));
+    }
+}
+
+void launch_segment_transform_df(const double *d, double2 *a, double2 *b, int log2n, const Twiddles &tw,
+                                 cudaStream_t s, double2 **result)
+{
+    const int64_t n = int64_t(1) << log2n;
+    dfc *da = reinterpret_cast<dfc *>(a), *db = reinterpret_cast<dfc *>(b), *r = nullptr;
+    k_real_to_dfc<<<1216, 256, 0, s>>>(d, da, n);
+    launched();
+    fft_passes<df>(da, db, log2n, -1, TwTab<df>{tw.lodf, tw.hidf, tw.shift, tw.log2n}, s, &r, 1, kDfLog2Radix);
+    k_dfc_to_double<<<1216, 256, 0, s>>>(r, n / 2 + 1);
+    launched();
+    *result = reinterpret_cast<double2 *>(r);
+}
+
 // lo[i] = exp(2 pi i i / 2^log2n), hi[i] = exp(2 pi i (i << shift) / 2^log2n), in FP64 and FP32
 __global__ void k_twiddle_tables(Twiddles t)
 {
@@ -122,6 +177,11 @@ __global__ void k_twiddle_tables(Twiddles t)
         float2 *f = i < nlo ? t.lo32 + i : t.hi32 + (i - nlo);
         *d = make_double2(c, s);
         *f = make_float2((float)c, (float)s);
+        if (t.lodf) {
+            dfc *q = i < nlo ? t.lodf + i : t.hidf + (i - nlo);
+            const float ch = __double2float_rn(c), sh = __double2float_rn(s);
+            *q = dfc{df{ch, __double2float_rn(c - (double)ch)}, df{sh, __double2float_rn(s - (double)sh)}};
+        }
     }
 }
 
@@ -132,16 +192,6 @@ void launch_twiddle_tables(const Twiddles &t, cudaStream_t s)
 }
 
 // -------------------------------------------------------- segment inputs ---
-__global__ void k_real_to_complex(const double *__restrict__ d, double2 *__restrict__ out, int64_t n)
-{
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-        out[j] = make_double2(d[j], 0.0);
-}
-void launch_real_to_complex(const double *d, double2 *out, int64_t n, cudaStream_t s)
-{
-    k_real_to_complex<<<1216, 256, 0, s>>>(d, out, n);
-    launched();
-}
 
 // amp_k = k^(-7/6) for k >= 1 (the Newtonian amplitude law without its
 // df^(-7/6) factor), amp_0 = 0.
