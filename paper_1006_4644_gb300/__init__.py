@@ -111,7 +111,10 @@ class Bank:
 
     def triggers(self, capacity: int = 1 << 20, allow_overflow: bool = False):
         """(triggers sorted by (tmpl, sample), exact total)."""
-        out = np.zeros(capacity, dtype=TRIGGER_DTYPE)
+        buf = getattr(self, "_trig_buf", None)
+        if buf is None or len(buf) < capacity:
+            buf = self._trig_buf = np.empty(capacity, dtype=TRIGGER_DTYPE)  # reused across calls
+        out = buf[:capacity]
         tot = C.c_int64()
         st = self._l.cui_triggers(self._h, out.ctypes.data, capacity, C.byref(tot))
         if not (allow_overflow and st == _lib.CUI_ERR_OVERFLOW):

@@ -1,11 +1,13 @@
 // C ABI of the bank matched filter (include/cui.h): argument checking, the
 // per-template constants, device buffers and the order of kernel launches.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -200,6 +202,10 @@ struct cui_bank_s {
     int64_t trig_cap = 0;
     unsigned long long *d_trig_count = nullptr;
     int *d_err = nullptr;
+    struct Stage {
+        int err, pad;
+        unsigned long long trig_count;
+    } *h_stage = nullptr; // pinned: read back with one synchronisation
     int32_t *d_order = nullptr;
     int64_t order_cap = 0;
     bool have_segment = false, have_peaks = false;
@@ -295,6 +301,7 @@ static void release(cui_bank b)
     for (cudaEvent_t e : b->pool) cudaEventDestroy(e);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->h_stage) cudaFreeHost(b->h_stage);
 }
 
 extern "C" const char *cui_last_error(void) { return g_err.c_str(); }
@@ -460,6 +467,7 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     chk(dalloc(&b->d_trig, b->trig_cap));
     chk(dalloc(&b->d_trig_count, 1));
     chk(dalloc(&b->d_err, 1));
+    chk(cudaMallocHost(&b->h_stage, sizeof(*b->h_stage)));
     chk(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
     b->h_c0.resize(nt);
     for (int64_t t = 0; t < nt; ++t) b->h_c0[t] = coef[t * kNB];
@@ -518,6 +526,32 @@ extern "C" void cui_bank_destroy(cui_bank b)
     delete b;
 }
 
+// True when every psd[k], lo <= k < hi, is finite and > 0.  A branch-free
+// scan split over a few host threads: it is memory-bound and runs while the
+// GPU transforms the strain.
+static bool psd_band_ok(const double *psd, int64_t lo, int64_t hi)
+{
+    constexpr int kThreads = 4;
+    unsigned bad[kThreads] = {};
+    auto scan = [&](int i) {
+        const int64_t a = lo + (hi - lo) * i / kThreads, e = lo + (hi - lo) * (i + 1) / kThreads;
+        unsigned acc = 0;
+        for (int64_t k = a; k < e; ++k) acc |= (unsigned)!(psd[k] > 0.0 && psd[k] <= DBL_MAX);
+        bad[i] = acc;
+    };
+    if (hi - lo < (int64_t(1) << 16)) {
+        for (int i = 0; i < kThreads; ++i) scan(i);
+    } else {
+        std::thread th[kThreads - 1];
+        for (int i = 1; i < kThreads; ++i) th[i - 1] = std::thread(scan, i);
+        scan(0);
+        for (auto &t : th) t.join();
+    }
+    unsigned any = 0;
+    for (unsigned v : bad) any |= v;
+    return any == 0;
+}
+
 extern "C" cui_status cui_segment_upload(cui_bank b, const double *strain, int64_t n, const double *psd,
                                          int64_t n_psd, int on_device)
 {
@@ -525,18 +559,23 @@ extern "C" cui_status cui_segment_upload(cui_bank b, const double *strain, int64
     if (!strain || !psd) return fail(CUI_ERR_ARG, "strain and psd must be non-NULL");
     if (n != b->n) return fail(CUI_ERR_ARG, "n = %lld differs from the bank's %lld", (long long)n, (long long)b->n);
     if (n_psd != b->nh + 1) return fail(CUI_ERR_ARG, "n_psd must be N/2 + 1 = %lld", (long long)(b->nh + 1));
-    if (!on_device) {
-        for (int64_t k = b->k_low; k < b->nh; ++k)
-            if (!(psd[k] > 0) || !std::isfinite(psd[k]))
-                return fail(CUI_ERR_ARG, "psd[%lld] must be finite and > 0 in the band", (long long)k);
-    }
     const cudaStream_t s = b->stream;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // The data transform needs only the strain: it is queued first, so that the
+    // host checks the PSD while the GPU transforms.
     CUI_TRY(cudaMemcpyAsync(b->d_strain, strain, sizeof(double) * b->n, kind, s), "strain copy");
-    CUI_TRY(cudaMemcpyAsync(b->d_psd, psd, sizeof(double) * (b->nh + 1), kind, s), "psd copy");
     Span span(b, 0);
     double2 *X = nullptr;
     launch_segment_transform_df(b->d_strain, b->d_fa, b->d_fb, b->log2n, b->tw, s, &X);
+    if (!on_device) {
+        if (!psd_band_ok(psd, b->k_low, b->nh)) {
+            b->have_segment = false; // the transform queued above replaced the previous segment's
+            for (int64_t k = b->k_low; k < b->nh; ++k)
+                if (!(psd[k] > 0) || !std::isfinite(psd[k]))
+                    return fail(CUI_ERR_ARG, "psd[%lld] must be finite and > 0 in the band", (long long)k);
+        }
+    }
+    CUI_TRY(cudaMemcpyAsync(b->d_psd, psd, sizeof(double) * (b->nh + 1), kind, s), "psd copy");
     b->d_X = X;
     launch_weighted_data(X, b->d_psd, b->d_amp, b->n, b->k_low, b->desc.sample_rate, b->d_scales, b->d_wbar,
                          b->d_dS, b->plain_fp64, s);
@@ -837,11 +876,19 @@ extern "C" cui_status cui_trace_read(cui_bank b, cui_trace_stat *host_out, int64
     return CUI_OK;
 }
 
-static cui_status sync_and_check(cui_bank b)
+// Wait for the bank's stream and read the device error word (and the trigger
+// count when asked) through the pinned staging area: one synchronisation.
+static cui_status sync_and_check(cui_bank b, unsigned long long *trig_count = nullptr)
 {
+    CUI_TRY(cudaMemcpyAsync(&b->h_stage->err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream),
+            "error word");
+    if (trig_count)
+        CUI_TRY(cudaMemcpyAsync(&b->h_stage->trig_count, b->d_trig_count, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, b->stream),
+                "trigger count");
     CUI_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
-    int err = 0;
-    CUI_TRY(cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error word");
+    if (trig_count) *trig_count = b->h_stage->trig_count;
+    const int err = b->h_stage->err;
     if (err) {
         cudaMemset(b->d_err, 0, sizeof(int));
         return fail(CUI_ERR_TIMEOUT, "a bounded device wait gave up (code %d)", err);
@@ -854,19 +901,18 @@ extern "C" cui_status cui_peaks(cui_bank b, cui_peak *host_out, int64_t count)
     if (!b || !host_out) return fail(CUI_ERR_ARG, "bank and host_out must be non-NULL");
     if (count < 0 || count > b->nt) return fail(CUI_ERR_ARG, "count must be in [0, n_templates]");
     if (!b->have_peaks) return fail(CUI_ERR_STATE, "no filter call kept its peaks in the handle");
-    cui_status st = sync_and_check(b);
-    if (st != CUI_OK) return st;
-    CUI_TRY(cudaMemcpy(host_out, b->d_peaks, sizeof(cui_peak) * count, cudaMemcpyDeviceToHost), "peaks copy");
-    return CUI_OK;
+    // the copy is queued behind the filter; the error word is read in the same synchronisation
+    CUI_TRY(cudaMemcpyAsync(host_out, b->d_peaks, sizeof(cui_peak) * count, cudaMemcpyDeviceToHost, b->stream),
+            "peaks copy");
+    return sync_and_check(b);
 }
 
 extern "C" cui_status cui_triggers(cui_bank b, cui_trigger *host_out, int64_t capacity, int64_t *n_total)
 {
     if (!b || !n_total) return fail(CUI_ERR_ARG, "bank and n_total must be non-NULL");
     if (capacity < 0 || (capacity > 0 && !host_out)) return fail(CUI_ERR_ARG, "bad capacity / host_out");
-    cui_status st = sync_and_check(b);
     unsigned long long cnt = 0;
-    CUI_TRY(cudaMemcpy(&cnt, b->d_trig_count, sizeof cnt, cudaMemcpyDeviceToHost), "trigger count");
+    cui_status st = sync_and_check(b, &cnt);
     *n_total = (int64_t)cnt;
     if (st != CUI_OK) return st;
     const int64_t have = std::min<int64_t>((int64_t)cnt, b->trig_cap);
