@@ -109,8 +109,8 @@ cui_status cui_bank_create(const cui_bank_desc *desc, const double *m1, const do
  * PSD S_k (n_psd = N/2 + 1 FP64 values, 1/Hz; only bins in [k_lo, N/2) are
  * read and must be finite and > 0).  on_device = 1 means both pointers are
  * device memory, 0 host memory (pinned host memory makes the copies
- * asynchronous).  Computes d~ in FP64, the noise-weighted data and every
- * template's sigma^2 on the device.
+ * asynchronous).  Computes d~ (double-float transform, FP64 result), the
+ * noise-weighted data and every template's sigma^2 on the device.
  * Errors: CUI_ERR_ARG (n != desc.n, n_psd != N/2 + 1, NULL pointers; a host
  * PSD bin in the band that is not finite and > 0, which leaves the bank
  * without a segment until the next successful upload; device PSDs are not
@@ -146,11 +146,26 @@ cui_status cui_peaks(cui_bank bank, cui_peak *host_out, int64_t count);
  * Paper: the candidate set {t_0^i} of step 4 and its reduction. */
 cui_status cui_triggers(cui_bank bank, cui_trigger *host_out, int64_t capacity, int64_t *n_total);
 
+/* Cross-template clustering of the last filter call's triggers: for each
+ * trigger window [valid_lo + m W, valid_lo + (m+1) W) (the same windows as
+ * the per-template triggers), the loudest trigger over all filtered
+ * templates; among equal rho the lowest sample, then the lowest template.
+ * Computed on the device while the triggers are compacted (one 128-bit
+ * compare-and-swap per trigger), so it is exact even when the trigger buffer
+ * overflowed.  Writes min(*n_total, capacity) records in increasing sample
+ * order (one per window that has a trigger) and the exact count to *n_total.
+ * Synchronises.  Errors: CUI_ERR_ARG, CUI_ERR_STATE (no filter call since the
+ * last upload), CUI_ERR_OVERFLOW (*n_total > capacity), CUI_ERR_TIMEOUT,
+ * CUI_ERR_CUDA.  Paper: the reduction of the per-template candidates to local
+ * maxima (Sec. "Matched filtering", final step) and the clustering it leaves
+ * to the CPU (Sec. "Pipeline main details"). */
+cui_status cui_cluster_triggers(cui_bank bank, cui_trigger *host_out, int64_t capacity, int64_t *n_total);
+
 /* sigma_t = sqrt(4 df sum_k |h~_k|^2 / S_k) of every template for the
  * uploaded PSD, to host_sigma[0 .. n_templates).  Synchronises.
  * Errors: CUI_ERR_STATE (no segment), CUI_ERR_CUDA.
- * Paper: the template normalisation of step 1 ("normalization", Sec.
- * "template generation and normalization"). */
+ * Paper: the template normalisation of step 1 (Sec. "template generation
+ * and normalization"). */
 cui_status cui_bank_sigma(cui_bank bank, double *host_sigma);
 
 /* Write template t as the fused path generates it: h~_k for k = 0 .. N/2 as
@@ -212,9 +227,9 @@ cui_status cui_trace_read(cui_bank bank, cui_trace_stat *host_out, int64_t capac
 /* ------------------------------------------------------------------------
  * Learned prescreen.  Ranks regions of the bank (groups of templates sorted
  * by chirp mass) from whitened band powers of a segment, so that likely
- * regions are filtered first.  The paper motivates it only in passing: at
- * ~10^6 templates brute force "is not the best solution" (introduction,
- * footnote).  Features: u_k = d~_k sqrt(4 df / S_k) on [f_low, fs/2) split
+ * regions are filtered first.  The paper motivates it only in passing: for
+ * banks of ~10^6 templates it doubts that exhaustive filtering is the right
+ * approach (introduction, footnote).  Features: u_k = d~_k sqrt(4 df / S_k) on [f_low, fs/2) split
  * into `bands` log-spaced bands; per band X_b(j) = sum_{k in band} u_k
  * exp(+2 pi i j k / N); F[b][m] = log(mean_{frame m} |X_b|^2 / (2 n_b)) over
  * N / frame frames.  Network: 4 conv1d layers of 32 channels (kernel 5,

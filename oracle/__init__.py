@@ -18,6 +18,9 @@ Each function names the part of the paper it follows:
   correlators c_+, c_x)
 * ``peak_triggers``    -- step 4 of the per-chunk loop (maximum above a
   threshold), with the window reading of "local maximum"
+* ``cluster_windows``  -- the final reduction of the per-template maxima
+  across the bank (Sec. "Matched filtering", last step), with the same window
+  reading: per window, the loudest trigger over all templates
 * ``fft`` / ``dft``    -- textbook radix-2 FFT and naive DFT used above
 
 Parity unpinned: the absolute constant of Psi (-pi/4 and the constant part of
@@ -228,3 +231,18 @@ def filter_bank(dtilde, psd, m1s, m2s, pn_x2: int, f_low: float, fs: float, n: i
 
     with ThreadPoolExecutor(max_workers=threads) as ex:
         return list(ex.map(one, range(len(m1s))))
+
+
+def cluster_windows(tmpl, sample, rho, lo: int, window: int):
+    """Cross-template clustering of trigger records: the windows
+    [lo + m W, lo + (m+1) W) are those of the per-template triggers; each
+    window keeps its record of largest rho, among equal rho the lowest sample,
+    then the lowest template.  Returns the kept record indices in increasing
+    sample order.  Plain loops; the records are few."""
+    best = {}
+    for i in range(len(tmpl)):
+        m = (int(sample[i]) - lo) // window
+        cand = (float(rho[i]), -int(sample[i]), -int(tmpl[i]))
+        if m not in best or cand > best[m][0]:
+            best[m] = (cand, i)
+    return [best[m][1] for m in sorted(best)]

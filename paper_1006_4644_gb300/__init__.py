@@ -122,6 +122,15 @@ class Bank:
         dev_cap = self.desc.trigger_capacity or (1 << 20)
         return out[: min(tot.value, capacity, dev_cap)].copy(), tot.value
 
+    def clustered_triggers(self, capacity: int = 1 << 20):
+        """Loudest trigger of each window over the whole bank (last filter call),
+        in increasing sample order; ties go to the lower sample, then template."""
+        out = np.empty(capacity, dtype=TRIGGER_DTYPE)
+        tot = C.c_int64()
+        _lib.check(self._l.cui_cluster_triggers(self._h, out.ctypes.data, capacity, C.byref(tot)),
+                   "cui_cluster_triggers")
+        return out[: tot.value].copy()
+
     def sigma(self):
         out = np.zeros(self.n_templates)
         _lib.check(self._l.cui_bank_sigma(self._h, out.ctypes.data), "cui_bank_sigma")

@@ -197,6 +197,8 @@ struct cui_bank_s {
     void *d_h = nullptr, *d_qa = nullptr, *d_qb = nullptr;
     double *d_acc = nullptr;
     Slot *d_pwin = nullptr;
+    Slot *d_cluster = nullptr; // [nwin] loudest trigger of each window over the bank (last filter call)
+    bool filtered = false;     // a filter call ran since the last upload
     // outputs
     cui_trigger *d_trig = nullptr;
     int64_t trig_cap = 0;
@@ -290,7 +292,7 @@ static void release(cui_bank b)
                     b->d_iota, b->d_strain, b->d_psd, b->d_amp, b->d_prefix, b->d_scan, b->d_fa, b->d_fb,
                     b->tw.lo64, b->tw.hi64, b->tw.lo32, b->tw.hi32, b->tw.lodf, b->tw.hidf,
                     b->d_wbar, b->d_dS, b->d_scales, b->d_basis, b->d_basis_df, b->d_kex, b->d_gexact, b->d_y,
-                    b->d_win, b->d_h, b->d_qa, b->d_qb, b->d_acc, b->d_pwin, b->d_trig, b->d_trig_count, b->d_err,
+                    b->d_win, b->d_h, b->d_qa, b->d_qb, b->d_acc, b->d_pwin, b->d_cluster, b->d_trig, b->d_trig_count, b->d_err,
                     b->d_order};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -466,6 +468,7 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     chk(dalloc(&b->tw.hidf, int64_t(1) << (b->log2n - b->tw.shift)));
     chk(dalloc(&b->d_trig, b->trig_cap));
     chk(dalloc(&b->d_trig_count, 1));
+    chk(dalloc(&b->d_cluster, std::max(1, b->nwin)));
     chk(dalloc(&b->d_err, 1));
     chk(cudaMallocHost(&b->h_stage, sizeof(*b->h_stage)));
     chk(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
@@ -584,6 +587,7 @@ extern "C" cui_status cui_segment_upload(cui_bank b, const double *strain, int64
                          b->d_invnorm, s);
     CUI_TRY(cudaGetLastError(), "cui_segment_upload");
     b->have_segment = true;
+    b->filtered = false;
     return CUI_OK;
 }
 
@@ -622,6 +626,15 @@ static FusedArgs fused_args(cui_bank b, const int32_t *order, int64_t base)
     return a;
 }
 
+// Zero the outputs that one filter call accumulates: the trigger count and the
+// bank-wide window slots.
+static cudaError_t reset_call_outputs(cui_bank b, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(b->d_trig_count, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cluster, 0, sizeof(Slot) * std::max(1, b->nwin), s);
+    return e;
+}
+
 static FinalizeArgs finalize_args(cui_bank b, const int32_t *d_ord, cui_peak *pout)
 {
     FinalizeArgs fa;
@@ -635,6 +648,8 @@ static FinalizeArgs finalize_args(cui_bank b, const int32_t *d_ord, cui_peak *po
     fa.trig = b->d_trig;
     fa.trig_cap = b->trig_cap;
     fa.trig_count = b->d_trig_count;
+    fa.cluster = b->d_cluster;
+    fa.err = b->d_err;
     fa.base = 0;
     fa.count = 0;
     return fa;
@@ -701,7 +716,7 @@ extern "C" cui_status cui_filter_bank(cui_bank b, const int32_t *order, int64_t 
             b->gexec = nullptr;
             const long long l0 = g_launches.load();
             CUI_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture");
-            cudaError_t e1 = cudaMemsetAsync(b->d_trig_count, 0, sizeof(unsigned long long), b->cap_stream);
+            cudaError_t e1 = reset_call_outputs(b, b->cap_stream);
             cudaError_t e2 = e1 == cudaSuccess ? enqueue_fused(b, d_ord, count, pout, b->cap_stream) : e1;
             cudaGraph_t graph = nullptr;
             cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &graph);
@@ -723,10 +738,10 @@ extern "C" cui_status cui_filter_bank(cui_bank b, const int32_t *order, int64_t 
         CUI_TRY(cudaGraphLaunch(b->gexec, s), "graph launch");
         launched((int)b->glaunches);
     } else if (b->fused) {
-        CUI_TRY(cudaMemsetAsync(b->d_trig_count, 0, sizeof(unsigned long long), s), "trigger reset");
+        CUI_TRY(reset_call_outputs(b, s), "trigger reset");
         CUI_TRY(enqueue_fused(b, d_ord, count, pout, s), "fused filter");
     } else {
-        CUI_TRY(cudaMemsetAsync(b->d_trig_count, 0, sizeof(unsigned long long), s), "trigger reset");
+        CUI_TRY(reset_call_outputs(b, s), "trigger reset");
         FinalizeArgs fa = finalize_args(b, d_ord, pout);
         PlainArgs a;
         a.mass = b->d_mass;
@@ -765,6 +780,7 @@ extern "C" cui_status cui_filter_bank(cui_bank b, const int32_t *order, int64_t 
         }
     }
     b->have_peaks = peaks_dev == nullptr;
+    b->filtered = true;
     return CUI_OK;
 }
 
@@ -929,6 +945,42 @@ extern "C" cui_status cui_triggers(cui_bank b, cui_trigger *host_out, int64_t ca
                     (long long)b->trig_cap);
     if ((int64_t)cnt > capacity)
         return fail(CUI_ERR_OVERFLOW, "%llu triggers exceed capacity %lld", cnt, (long long)capacity);
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_cluster_triggers(cui_bank b, cui_trigger *host_out, int64_t capacity, int64_t *n_total)
+{
+    if (!b || !n_total) return fail(CUI_ERR_ARG, "bank and n_total must be non-NULL");
+    if (capacity < 0 || (capacity > 0 && !host_out)) return fail(CUI_ERR_ARG, "bad capacity / host_out");
+    if (!b->filtered) return fail(CUI_ERR_STATE, "no filter call since the last upload");
+    const int nw = std::max(1, b->nwin);
+    std::vector<Slot> h(nw);
+    CUI_TRY(cudaMemcpyAsync(h.data(), b->d_cluster, sizeof(Slot) * nw, cudaMemcpyDeviceToHost, b->stream),
+            "cluster copy");
+    cui_status st = sync_and_check(b);
+    if (st != CUI_OK) return st;
+    int64_t n = 0;
+    for (int w = 0; w < nw; ++w) {
+        const Slot &sl = h[w];
+        if (sl.key == 0ull) continue;
+        if (n < capacity) {
+            cui_trigger tr;
+            const uint32_t r2 = (uint32_t)(sl.key >> 32);
+            float rho2, ph;
+            std::memcpy(&rho2, &r2, 4);
+            std::memcpy(&ph, &sl.phase_bits, 4);
+            tr.tmpl = (int32_t)(0xFFFFFFFFu - sl.pad);
+            tr.pad = 0;
+            tr.sample = (int64_t)(0xFFFFFFFFu - (uint32_t)(sl.key & 0xFFFFFFFFull));
+            tr.snr = std::sqrt(rho2);
+            tr.phase = ph;
+            host_out[n] = tr;
+        }
+        ++n;
+    }
+    *n_total = n;
+    if (n > capacity) return fail(CUI_ERR_OVERFLOW, "%lld clustered triggers exceed capacity %lld", (long long)n,
+                                  (long long)capacity);
     return CUI_OK;
 }
 

@@ -372,6 +372,34 @@ __device__ __forceinline__ void slot_max(Slot *s, unsigned long long key, float 
     atomicOr(err, 2);
 }
 
+// Bank-wide window slot: raise it to (key, template, phase) if (key, lower
+// template) is larger; the template is kept as 0xFFFFFFFF - tmpl in `pad`, so
+// among equal keys the lowest template wins.  Same bounded CAS as slot_max.
+__device__ __forceinline__ void cluster_max(Slot *s, unsigned long long key, uint32_t tmpl, uint32_t phase_bits,
+                                            int *err)
+{
+    const unsigned long long tinv = (unsigned long long)(0xFFFFFFFFu - tmpl);
+    const unsigned long long new_hi = (tinv << 32) | (unsigned long long)phase_bits;
+    unsigned long long cur_lo = *(volatile unsigned long long *)&s->key;
+    unsigned long long cur_hi = *(volatile unsigned long long *)&s->phase_bits;
+    for (int it = 0; it < (1 << 20); ++it) {
+        if (cur_lo > key || (cur_lo == key && (cur_hi >> 32) >= tinv)) return;
+        unsigned long long old_lo, old_hi;
+        asm volatile("{\n\t.reg .b128 d, c, n;\n\t"
+                     "mov.b128 c, {%2, %3};\n\t"
+                     "mov.b128 n, {%4, %5};\n\t"
+                     "atom.global.cas.b128 d, [%6], c, n;\n\t"
+                     "mov.b128 {%0, %1}, d;\n\t}"
+                     : "=l"(old_lo), "=l"(old_hi)
+                     : "l"(cur_lo), "l"(cur_hi), "l"(key), "l"(new_hi), "l"(s)
+                     : "memory");
+        if (old_lo == cur_lo && old_hi == cur_hi) return;
+        cur_lo = old_lo;
+        cur_hi = old_hi;
+    }
+    atomicOr(err, 2);
+}
+
 // Warp-wide maximum of (key, zr, zi) by key.
 __device__ __forceinline__ void warp_max_key(unsigned long long &key, float &zr, float &zi)
 {

@@ -796,6 +796,7 @@ __global__ void k_finalize_windows(const FinalizeArgs a)
         decode(sl, tr.sample, tr.snr, tr.phase);
         const unsigned long long pos = atomicAdd(a.trig_count, 1ull);
         if (pos < (unsigned long long)a.trig_cap) a.trig[pos] = tr;
+        cluster_max(a.cluster + (i % a.nwin), sl.key, (uint32_t)tr.tmpl, sl.phase_bits, a.err);
         Slot zero = {0ull, 0u, 0u};
         a.win[i] = zero;
     }

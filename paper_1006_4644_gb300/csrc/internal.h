@@ -114,6 +114,8 @@ struct FinalizeArgs {
     cui_trigger *trig;       // [cap]
     int64_t trig_cap;
     unsigned long long *trig_count;
+    Slot *cluster;           // [nwin] loudest trigger of each window over the bank
+    int *err;
 };
 cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s);
 

@@ -1,9 +1,9 @@
 // Learned prescreen: whitened band-power features of a segment, a small
 // 1D-conv + MLP network that scores bank regions, and its training (forward,
 // backward, deterministic gradient reduction, Adam), all in hand-written
-// kernels.  The paper motivates it only in passing (at ~10^6 templates "the
-// brute force is not the best solution", introduction footnote); its shape
-// follows the stated configuration: 4 conv1d layers of 32 channels (kernel 5,
+// kernels.  The paper motivates it only in passing (for ~10^6 templates it
+// doubts exhaustive filtering, introduction footnote); its shape follows the
+// stated configuration: 4 conv1d layers of 32 channels (kernel 5,
 // stride 1 then 2, zero padding 2, ReLU), per-channel mean and max pooling,
 // MLP 64 -> 128 -> regions, BF16 weights with FP32 accumulation.
 #include <cuda_bf16.h>

@@ -1,0 +1,128 @@
+"""Cross-template trigger clustering on the GPU (cui_cluster_triggers): the
+device result equals the oracle's clustering of the device's own triggers bit
+for bit, matches the oracle's clustering of its own FP64 triggers (c8 rule for
+near-ties), and stays exact through a trigger-buffer overflow, template
+subsets and the per-template path."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import AMBIG, RTOL, make_segment, oracle_series
+
+pytestmark = pytest.mark.gpu
+
+W = synth.WORKLOADS["seg16s_bank64_pn2"]
+THR, WIN = 5.0, 2048
+
+
+@pytest.fixture(scope="module")
+def seg():
+    from paper_1006_4644_gb300 import build
+
+    build.build()
+    oracle.build()
+    return make_segment(W)
+
+
+def _bank(flags=0, cap=0, window=WIN):
+    from paper_1006_4644_gb300 import Bank
+
+    m1, m2 = W.masses()
+    return Bank(m1, m2, n=W.n, fs=W.fs, f_low=W.f_low, pn_x2=W.pn_x2, flags=flags, snr_threshold=THR,
+                window=window, trigger_capacity=cap)
+
+
+def _self_consistent(trig, clus, lo=0, window=WIN):
+    keep = oracle.cluster_windows(trig["tmpl"], trig["sample"], trig["snr"], lo, window)
+    assert np.array_equal(clus, trig[keep])
+
+
+@pytest.mark.parametrize("flags", [0, 4], ids=["fused", "plain"])
+def test_cluster_of_own_triggers(seg, flags):
+    strain, psd, _, _ = seg
+    with _bank(flags) as b:
+        b.upload(strain, psd)
+        b.filter()
+        trig, total = b.triggers()
+        clus = b.clustered_triggers()
+    assert total == len(trig) > len(clus) > 0
+    assert np.all(np.diff(clus["sample"]) > 0)
+    _self_consistent(trig, clus)
+
+
+def test_cluster_matches_the_oracle(seg):
+    strain, psd, dt, plan = seg
+    m1, m2 = W.masses()
+    # the oracle's per-template window maxima above threshold, then its clustering
+    rho_all = []
+    recs = []  # (tmpl, sample, rho)
+    for t in range(W.n_templates):
+        _, rho2, _ = oracle_series(dt, psd, m1[t], m2[t], W.pn_x2, W.f_low, W.fs, W.n)
+        rho = np.sqrt(rho2)
+        rho_all.append(rho)
+        for m in range(W.n // WIN):
+            j = m * WIN + int(np.argmax(rho[m * WIN:(m + 1) * WIN]))
+            if rho[j] > THR:
+                recs.append((t, j, float(rho[j])))
+    keep = oracle.cluster_windows([r[0] for r in recs], [r[1] for r in recs], [r[2] for r in recs], 0, WIN)
+    want = [recs[i] for i in keep]
+    with _bank() as b:
+        b.upload(strain, psd)
+        b.filter()
+        got = b.clustered_triggers()
+    assert len(got) == len(want)
+    ambiguous = 0
+    for g, (t, s, r) in zip(got, want):
+        assert g["sample"] // WIN == s // WIN
+        assert abs(g["snr"] / r - 1) < RTOL
+        if (int(g["tmpl"]), int(g["sample"])) != (t, s):
+            # accepted only where the oracle's rho at the GPU's pick is within AMBIG of the window's maximum
+            assert rho_all[int(g["tmpl"])][int(g["sample"])] >= r * (1 - AMBIG), (g, (t, s, r))
+            ambiguous += 1
+    assert ambiguous <= 2
+    # the injection's window is led by a template peaking at the injection
+    j_inj, snr_inj = int(plan[1][0]), float(plan[2][0])
+    lead = got[got["sample"] // WIN == j_inj // WIN]
+    assert len(lead) == 1 and abs(int(lead[0]["sample"]) - j_inj) <= WIN // 8
+    assert lead[0]["snr"] >= 0.9 * snr_inj
+
+
+def test_cluster_is_exact_through_overflow(seg):
+    strain, psd, _, _ = seg
+    with _bank() as b:
+        b.upload(strain, psd)
+        b.filter()
+        ref = b.clustered_triggers()
+    with _bank(cap=4) as b:
+        b.upload(strain, psd)
+        b.filter()
+        _, total = b.triggers(capacity=4, allow_overflow=True)
+        assert total > 4
+        assert np.array_equal(b.clustered_triggers(), ref)
+
+
+def test_cluster_of_a_subset_and_errors(seg):
+    from paper_1006_4644_gb300 import CuiError, _lib
+
+    strain, psd, _, _ = seg
+    order = np.arange(3, W.n_templates, 5)
+    with _bank() as b:
+        with pytest.raises(CuiError) as e:
+            b.clustered_triggers()
+        assert e.value.status == _lib.CUI_ERR_STATE
+        b.upload(strain, psd)
+        with pytest.raises(CuiError) as e:
+            b.clustered_triggers()  # uploaded but not filtered
+        assert e.value.status == _lib.CUI_ERR_STATE
+        b.filter(order)
+        trig, _ = b.triggers()
+        clus = b.clustered_triggers()
+        assert set(clus["tmpl"].tolist()) <= set(order.tolist())
+        _self_consistent(trig, clus)
+        b.filter()
+        assert len(b.clustered_triggers()) > 1
+        with pytest.raises(CuiError) as e:
+            b.clustered_triggers(capacity=1)
+        assert e.value.status == _lib.CUI_ERR_OVERFLOW
