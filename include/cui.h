@@ -161,6 +161,25 @@ cui_status cui_triggers(cui_bank bank, cui_trigger *host_out, int64_t capacity, 
  * to the CPU (Sec. "Pipeline main details"). */
 cui_status cui_cluster_triggers(cui_bank bank, cui_trigger *host_out, int64_t capacity, int64_t *n_total);
 
+/* Signal-consistency (chi^2) test at n triggers (host records, e.g. from
+ * cui_triggers; only tmpl and sample are read) against the uploaded segment.
+ * The template's band [k_lo, k_hi) is split into `bands` sub-bands of equal
+ * template power, edges k_l = min{k : Pw(k) >= (l/bands) Pw(k_hi)} with
+ * Pw(k) = sum_{k_lo <= j < k} |h~_j|^2 / S_j; with the sub-band correlators
+ * z_l (z restricted to band l, at the trigger's sample) and z = sum_l z_l,
+ *   chi^2 = bands sum_l |z_l - z / bands|^2 / sigma^2,
+ * about 2 bands - 2 in Gaussian noise and ~0 for the exact template.
+ * host_chisq[i] receives chi^2 of trigger i; host_rho (nullable) the rho
+ * recomputed from the same sums.  Fused banks only.  Synchronises.
+ * Errors: CUI_ERR_ARG (bands outside [1, 64], a template or sample out of
+ * range, NULL pointers), CUI_ERR_STATE (plain bank, no segment),
+ * CUI_ERR_CUDA, CUI_ERR_TIMEOUT.  Paper: the chi^2 discrimination against
+ * non-Gaussian noise listed among the pipeline's future work (Sec.
+ * "Conclusions"), in the equal-power sub-band form of the matched-filter
+ * literature it builds on. */
+cui_status cui_trigger_chisq(cui_bank bank, int32_t bands, const cui_trigger *trig, int64_t n, float *host_chisq,
+                             float *host_rho);
+
 /* sigma_t = sqrt(4 df sum_k |h~_k|^2 / S_k) of every template for the
  * uploaded PSD, to host_sigma[0 .. n_templates).  Synchronises.
  * Errors: CUI_ERR_STATE (no segment), CUI_ERR_CUDA.

@@ -21,6 +21,9 @@ Each function names the part of the paper it follows:
 * ``cluster_windows``  -- the final reduction of the per-template maxima
   across the bank (Sec. "Matched filtering", last step), with the same window
   reading: per window, the loudest trigger over all templates
+* ``chisq``            -- the chi-squared signal-consistency test that the
+  paper lists as future work (Sec. "Conclusions"), in its equal-power
+  sub-band form: chi^2 = p sum_l |z_l - z/p|^2 / sigma^2
 * ``fft`` / ``dft``    -- textbook radix-2 FFT and naive DFT used above
 
 Parity unpinned: the absolute constant of Psi (-pi/4 and the constant part of
@@ -246,3 +249,28 @@ def cluster_windows(tmpl, sample, rho, lo: int, window: int):
         if m not in best or cand > best[m][0]:
             best[m] = (cand, i)
     return [best[m][1] for m in sorted(best)]
+
+
+def chisq(dtilde, psd, m1: float, m2: float, pn_x2: int, f_low: float, fs: float, n: int, samples, bands: int):
+    """chi^2 and rho of one template at the given samples.  The band
+    [k_lo, k_hi) is split at k_l = min{k : Pw(k) >= (l/p) Pw(k_hi)}, Pw(k) =
+    sum_{k_lo <= j < k} |h~_j|^2 / S_j; z_l(s) = 4 df sum_{k in band l}
+    d~_k conj(h~_k) / S_k exp(2 pi i k s / N) by direct summation; z = sum_l z_l;
+    chi^2 = p sum_l |z_l - z/p|^2 / sigma^2 and rho = |z| / sigma."""
+    h, k_lo, k_hi = spa_template(m1, m2, pn_x2, f_low, fs, n)
+    psd = _f64(psd)
+    df = fs / n
+    k = np.arange(k_lo, k_hi)
+    terms = 4.0 * df * np.asarray(dtilde)[k_lo:k_hi] * np.conj(h[k_lo:k_hi]) / psd[k_lo:k_hi]
+    power = np.abs(h[k_lo:k_hi]) ** 2 / psd[k_lo:k_hi]
+    pw = np.concatenate([[0.0], np.cumsum(power)])  # pw[i] = Pw(k_lo + i)
+    edges = [0] + [int(np.searchsorted(pw, pw[-1] * l / bands, side="left")) for l in range(1, bands)] + [len(k)]
+    s2 = sigma2(h, psd, fs, n, k_lo, k_hi)
+    chi, rho = [], []
+    for s in samples:
+        ph = np.exp(2j * np.pi * ((k * int(s)) % n) / n)
+        zl = np.array([np.sum(terms[edges[l]:edges[l + 1]] * ph[edges[l]:edges[l + 1]]) for l in range(bands)])
+        z = zl.sum()
+        chi.append(bands * np.sum(np.abs(zl - z / bands) ** 2) / s2)
+        rho.append(abs(z) / np.sqrt(s2))
+    return np.array(chi), np.array(rho)

@@ -131,6 +131,16 @@ class Bank:
                    "cui_cluster_triggers")
         return out[: tot.value].copy()
 
+    def trigger_chisq(self, trig, bands: int = 16):
+        """(chi^2, rho) at trigger records (structured array as returned by
+        ``triggers``): the equal-power sub-band signal-consistency test."""
+        trig = np.ascontiguousarray(trig, dtype=TRIGGER_DTYPE)
+        chi = np.zeros(len(trig), dtype=np.float32)
+        rho = np.zeros(len(trig), dtype=np.float32)
+        _lib.check(self._l.cui_trigger_chisq(self._h, int(bands), trig.ctypes.data, len(trig), chi.ctypes.data,
+                                             rho.ctypes.data), "cui_trigger_chisq")
+        return chi, rho
+
     def sigma(self):
         out = np.zeros(self.n_templates)
         _lib.check(self._l.cui_bank_sigma(self._h, out.ctypes.data), "cui_bank_sigma")

@@ -984,6 +984,39 @@ extern "C" cui_status cui_cluster_triggers(cui_bank b, cui_trigger *host_out, in
     return CUI_OK;
 }
 
+extern "C" cui_status cui_trigger_chisq(cui_bank b, int32_t bands, const cui_trigger *trig, int64_t n,
+                                        float *host_chisq, float *host_rho)
+{
+    if (!b) return fail(CUI_ERR_ARG, "bank is NULL");
+    if (bands < 1 || bands > kChisqMaxBands) return fail(CUI_ERR_ARG, "bands must be in [1, %d]", kChisqMaxBands);
+    if (n < 0 || n > (int64_t(1) << 30) || (n > 0 && (!trig || !host_chisq)))
+        return fail(CUI_ERR_ARG, "bad trigger count or NULL pointers");
+    if (!b->fused) return fail(CUI_ERR_STATE, "the chi^2 test needs the fused path (N >= 2^12, no CUI_PLAIN)");
+    if (!b->have_segment) return fail(CUI_ERR_STATE, "no segment uploaded");
+    if (n == 0) return CUI_OK;
+    std::vector<int2> h(n);
+    for (int64_t i = 0; i < n; ++i) {
+        if (trig[i].tmpl < 0 || trig[i].tmpl >= b->nt || trig[i].sample < 0 || trig[i].sample >= b->n)
+            return fail(CUI_ERR_ARG, "trigger %lld: template or sample out of range", (long long)i);
+        h[i] = make_int2(trig[i].tmpl, (int)trig[i].sample);
+    }
+    const cudaStream_t s = b->stream;
+    int2 *d_trig = nullptr;
+    float *d_out = nullptr;
+    cudaError_t e = cudaMalloc(&d_trig, sizeof(int2) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(float) * 2 * n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_trig, h.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_chisq(fused_args(b, b->d_iota, 0), b->d_prefix, d_trig, (int)n, bands, d_out, d_out + n, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_chisq, d_out, sizeof(float) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && host_rho)
+        e = cudaMemcpyAsync(host_rho, d_out + n, sizeof(float) * n, cudaMemcpyDeviceToHost, s);
+    cui_status st = e == cudaSuccess ? sync_and_check(b) : cuda_fail(e, "chi^2");
+    cudaFree(d_trig);
+    cudaFree(d_out);
+    return st;
+}
+
 extern "C" cui_status cui_bank_sigma(cui_bank b, double *host_sigma)
 {
     if (!b || !host_sigma) return fail(CUI_ERR_ARG, "bank and host_sigma must be non-NULL");

@@ -756,6 +756,118 @@ cudaError_t launch_template_out(const FusedArgs &a, int t, const double *amp, do
     return cudaGetLastError();
 }
 
+// --------------------------------------------------------- chi^2 veto ----
+// Signal-consistency test at a trigger (template t, sample s): the template's
+// band [k_low, k_hi) is split into P sub-bands of equal template power, edges
+// k_l = min{k : Pw[k] >= (l/P) Pw[k_hi]} from the prefix sums Pw of
+// |h~_k|^2 / S_k; the sub-band correlators z_l(s) = sum_{k in band l} q_k
+// exp(2 pi i k s / N) are summed directly at s, with q_k generated exactly as
+// pass 1 generates it (same anchors, cubic and exact-phase table); then
+// chi^2 = P sum_l |z_l - z/P|^2 / sigma^2 with z = sum_l z_l.
+constexpr int kChisqWarps = 8;
+
+__global__ void __launch_bounds__(kChisqWarps * 32) k_chisq(const FusedArgs p, const double *prefix, const int2 *trig,
+                                                           int P, float *chisq, float *rho)
+{
+    __shared__ int bnd[kChisqMaxBands + 1];
+    __shared__ float2 cdf[kNB];
+    __shared__ float2 part[kChisqWarps];
+    __shared__ float2 zl[kChisqMaxBands];
+    const int i = blockIdx.x;
+    const int t = trig[i].x;
+    const int64_t smp = trig[i].y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int klo = p.k_low, khi = max(p.khi[t], klo), kex = p.kex[t];
+    const int C = p.ccols;
+    const int64_t N = p.n;
+    if (threadIdx.x < kNB) cdf[threadIdx.x] = p.coef_df[(int64_t)t * kNB + threadIdx.x];
+    if (threadIdx.x <= P) {
+        const int l = threadIdx.x;
+        int e = l == 0 ? klo : khi;
+        if (l > 0 && l < P) {
+            // smallest k in [klo, khi] with prefix[k] >= (l/P) prefix[khi] (prefix[klo] = 0)
+            const double target = prefix[khi] * (double)l / (double)P;
+            int lo = klo, hi = khi;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (prefix[mid] >= target) hi = mid;
+                else lo = mid + 1;
+            }
+            e = lo;
+        }
+        bnd[l] = e;
+    }
+    __syncthreads();
+    for (int l = 0; l < P; ++l) {
+        const int ka = bnd[l], kb = bnd[l + 1];
+        float2 acc = make_float2(0.f, 0.f);
+        if (kb > ka) {
+            const int B0 = ka / C, B1 = (kb - 1) / C; // blocks of C bins, anchored at their centres
+            for (int base = B0 + warp * 32; base <= B1; base += kChisqWarps * 32) {
+                // lane j evaluates the anchor of block base + j; the warp then sweeps those blocks
+                float4 anc = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (base + lane <= B1)
+                    anc = anchor_eval(p, t, base + lane, (float)((int64_t)(base + lane) * C + C / 2));
+                const int nb = min(32, B1 - base + 1);
+                for (int j = 0; j < nb; ++j) {
+                    const float4 a = make_float4(__shfl_sync(0xffffffffu, anc.x, j), __shfl_sync(0xffffffffu, anc.y, j),
+                                                 __shfl_sync(0xffffffffu, anc.z, j), __shfl_sync(0xffffffffu, anc.w, j));
+                    const int B = base + j;
+                    for (int x = lane; x < C; x += 32) {
+                        const int k = B * C + x;
+                        if (k < ka || k >= kb) continue;
+                        const float2 w = p.wbar[k];
+                        const float2 q = k < kex ? rotate(phase_exact(cdf, p.gexact + (int64_t)k * kNB), w)
+                                                 : gen_bin(a, (float)(x - C / 2), w);
+                        // exp(2 pi i k s / N), from k s mod N (exact in integers)
+                        float fr = (float)(((int64_t)k * smp) & (N - 1)) / (float)N;
+                        fr -= rintf(fr);
+                        float sn, cs;
+                        __sincosf(6.283185307179586f * fr, &sn, &cs);
+                        const float2 v = cmul(q, make_float2(cs, sn));
+                        acc.x += v.x;
+                        acc.y += v.y;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if (lane == 0) part[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float2 z = make_float2(0.f, 0.f);
+            for (int w8 = 0; w8 < kChisqWarps; ++w8) z = z + part[w8];
+            zl[l] = z;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        float2 z = make_float2(0.f, 0.f);
+        for (int l = 0; l < P; ++l) z = z + zl[l];
+        const float inv = p.invnorm[t];
+        float c2 = 0.f;
+        for (int l = 0; l < P; ++l) {
+            const float dx = zl[l].x - z.x / P, dy = zl[l].y - z.y / P;
+            c2 += dx * dx + dy * dy;
+        }
+        chisq[i] = P * c2 * inv;
+        if (rho) rho[i] = sqrtf((z.x * z.x + z.y * z.y) * inv);
+    }
+}
+
+cudaError_t launch_chisq(const FusedArgs &a, const double *prefix, const int2 *trig, int n, int bands, float *chisq,
+                         float *rho, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_chisq<<<n, kChisqWarps * 32, 0, s>>>(a, prefix, trig, bands, chisq, rho);
+    launched();
+    return cudaGetLastError();
+}
+
 // -------------------------------------------------------------- finalize ---
 __device__ __forceinline__ void decode(const Slot &sl, int64_t &sample, float &snr, float &phase)
 {

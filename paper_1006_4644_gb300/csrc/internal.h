@@ -99,6 +99,10 @@ size_t fused_pass1_smem(int n1, int ccols);
 size_t fused_pass2_smem(int n2, int rpc);
 cudaError_t launch_pass1(const FusedArgs &a, int count, cudaStream_t s);
 cudaError_t launch_pass2(const FusedArgs &a, int count, cudaStream_t s);
+constexpr int kChisqMaxBands = 64;
+// chi^2 (and rho) of n triggers (tmpl, sample) with `bands` sub-bands
+cudaError_t launch_chisq(const FusedArgs &a, const double *prefix, const int2 *trig, int n, int bands, float *chisq,
+                         float *rho, cudaStream_t s);
 cudaError_t launch_template_out(const FusedArgs &a, int t, const double *amp, double dfac, float2 *out,
                                 cudaStream_t s);
 
