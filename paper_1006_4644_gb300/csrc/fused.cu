@@ -435,17 +435,10 @@ __device__ __noinline__ void p2_emit(Slot *win, int64_t s, int64_t lo, int64_t w
     slot_max(win + (int)((s - lo) / window), make_key(r2, (uint32_t)s), atan2f(zi, zr), err);
 }
 
-// Running maximum of |z|^2 over one lane's outputs d of a row.
-struct Best {
-    float m, zr, zi;
-    int d;
-};
-
-// Visit this thread's outputs d = j + r L/RL in increasing d, so the strict
-// '>' keeps the lowest sample among equal |z|^2.  CHECK limits d to
-// [dlo, dhi) (rows that leave the valid sample range).
+// Each lane's maximum of |z|^2 over this thread's outputs d = j + r L/RL of
+// its row; CHECK limits d to [dlo, dhi) (rows that leave the valid range).
 template <int L, int RL, bool CHECK, int PPT, typename E>
-__device__ __forceinline__ void p2_scan(const E *v, int lt, Best *b, const int *dlo, const int *dhi)
+__device__ __forceinline__ void p2_max(const E *v, int lt, float *m, const int *dlo, const int *dhi)
 {
     constexpr int TPR = L / PPT, TL = PPT / RL, NL = lanes_of<E>;
 #pragma unroll
@@ -453,16 +446,37 @@ __device__ __forceinline__ void p2_scan(const E *v, int lt, Best *b, const int *
 #pragma unroll
         for (int i = 0; i < TL; ++i) {
             const int d = lt + i * TPR + r * (L / RL);
-            const float2 m = abs2(v[i * RL + r]);
+            const float2 a = abs2(v[i * RL + r]);
+#pragma unroll
+            for (int l = 0; l < NL; ++l)
+                if (!CHECK || (d >= dlo[l] && d < dhi[l])) m[l] = fmaxf(m[l], l ? a.y : a.x);
+        }
+}
+
+// The lowest sample (and its z) among this thread's in-range outputs whose
+// |z|^2 equals M; run only by threads that hold the CTA's maximum.
+template <int L, int RL, int PPT, typename E>
+__device__ __forceinline__ int64_t p2_find(const E *v, int lt, float M, const int64_t *cl, int n1, const int *dlo,
+                                           const int *dhi, float2 &zb)
+{
+    constexpr int TPR = L / PPT, TL = PPT / RL, NL = lanes_of<E>;
+    int64_t best = INT64_MAX;
+#pragma unroll
+    for (int r = 0; r < RL; ++r)
+#pragma unroll
+        for (int i = 0; i < TL; ++i) {
+            const int d = lt + i * TPR + r * (L / RL);
+            const float2 a = abs2(v[i * RL + r]);
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
-                const float ml = l ? m.y : m.x;
-                if (ml > b[l].m && (!CHECK || (d >= dlo[l] && d < dhi[l]))) {
-                    const float2 z = lane(v[i * RL + r], l);
-                    b[l] = {ml, z.x, z.y, d};
+                const int64_t s = cl[l] + (int64_t)n1 * d;
+                if ((l ? a.y : a.x) == M && d >= dlo[l] && d < dhi[l] && s < best) {
+                    best = s;
+                    zb = lane(v[i * RL + r], l);
                 }
             }
         }
+    return best;
 }
 
 // Grid (rows / RPC, B), rows = n1 (or n1 / 2 row pairs when PAIR).  RPC rows
@@ -485,8 +499,7 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
     E *sm = reinterpret_cast<E *>(sm4);
     __shared__ float2 tw1[R0 * R1]; // stage-1 twiddles (sub-transform size R0)
     __shared__ float2 tw2[R3 > 1 ? R0 * R1 * R2 : 1]; // stage-2 twiddles of four-stage rows
-    __shared__ unsigned long long s_key[NW];
-    __shared__ float s_zr[NW], s_zi[NW];
+    __shared__ float s_max[NW];
     const int tid = threadIdx.x;
     const int rr = tid / TPR, lt = tid % TPR;
     const int y = blockIdx.y;
@@ -536,14 +549,16 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
     p2_stage<L, RL, NSL, R2 == 1, PPT>(v, row, lt, tw1);
 
     // Epilogue.  Output d of lane l is sample s = c_l + n1 d with
-    // c_l = c + l n1/2; |z|^2 is compared before the (positive) scaling.
+    // c_l = c + l n1/2; |z|^2 is compared before the (positive) scaling.  The
+    // CTA's maximum of |z|^2 is reduced first; only the threads that hold it
+    // then look for their lowest sample with it and raise the peak slot.
     const float inv = p.invnorm[t];
     const int n1 = p.n1;
     const int64_t lo = p.lo, hi = p.hi;
     int64_t cl[NL];
     int dlo[NL], dhi[NL];
     bool full = true;
-    Best b[NL];
+    float m[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
         cl[l] = c + (int64_t)l * (n1 / 2);
@@ -554,14 +569,14 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
             dlo[l] = (int)max((int64_t)0, (lo - cl[l] + n1 - 1) / n1);
             dhi[l] = (int)min((int64_t)L, hi > cl[l] ? (hi - cl[l] + n1 - 1) / n1 : (int64_t)0);
         }
-        b[l] = {-1.f, 0.f, 0.f, 0};
+        m[l] = -1.f;
     }
-    if (full) p2_scan<L, RL, false, PPT>(v, lt, b, dlo, dhi);
-    else p2_scan<L, RL, true, PPT>(v, lt, b, dlo, dhi);
+    if (full) p2_max<L, RL, false, PPT>(v, lt, m, dlo, dhi);
+    else p2_max<L, RL, true, PPT>(v, lt, m, dlo, dhi);
 
-    float mx = b[0].m;
+    float mx = m[0];
 #pragma unroll
-    for (int l = 1; l < NL; ++l) mx = fmaxf(mx, b[l].m);
+    for (int l = 1; l < NL; ++l) mx = fmaxf(mx, m[l]);
     if (mx * inv > p.thr2) {
         constexpr int TL = PPT / RL;
         Slot *win = p.win + (size_t)y * p.nwin;
@@ -570,10 +585,10 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
 #pragma unroll
             for (int i = 0; i < TL; ++i) {
                 const int d = lt + i * TPR + r * (L / RL);
-                const float2 m = abs2(v[i * RL + r]);
+                const float2 a = abs2(v[i * RL + r]);
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
-                    const float r2 = (l ? m.y : m.x) * inv;
+                    const float r2 = (l ? a.y : a.x) * inv;
                     if (r2 > p.thr2 && d >= dlo[l] && d < dhi[l]) {
                         const float2 z = lane(v[i * RL + r], l);
                         p2_emit(win, cl[l] + (int64_t)n1 * d, lo, p.window, r2, z.x, z.y, p.err);
@@ -581,32 +596,19 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
                 }
             }
     }
-    unsigned long long key = 0ull;
-    float bzr = 0.f, bzi = 0.f;
+    float wm = mx;
 #pragma unroll
-    for (int l = 0; l < NL; ++l) {
-        const unsigned long long k =
-            b[l].m >= 0.f ? make_key(b[l].m * inv, (uint32_t)(cl[l] + (int64_t)n1 * b[l].d)) : 0ull;
-        if (k > key) {
-            key = k;
-            bzr = b[l].zr;
-            bzi = b[l].zi;
-        }
-    }
-    warp_max_key(key, bzr, bzi);
+    for (int off = 16; off > 0; off >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, off));
     const int lane_id = tid & 31, wid = tid >> 5;
-    if (lane_id == 0) {
-        s_key[wid] = key;
-        s_zr[wid] = bzr;
-        s_zi[wid] = bzi;
-    }
+    if (lane_id == 0) s_max[wid] = wm;
     __syncthreads();
-    if (wid == 0) {
-        key = lane_id < NW ? s_key[lane_id] : 0ull;
-        bzr = lane_id < NW ? s_zr[lane_id] : 0.f;
-        bzi = lane_id < NW ? s_zi[lane_id] : 0.f;
-        warp_max_key(key, bzr, bzi);
-        if (lane_id == 0 && key != 0ull) slot_max(p.peak + t, key, atan2f(bzi, bzr), p.err);
+    float M = s_max[0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) M = fmaxf(M, s_max[w]);
+    if (M >= 0.f && mx == M) {
+        float2 zb = make_float2(0.f, 0.f);
+        const int64_t sb = p2_find<L, RL, PPT>(v, lt, M, cl, n1, dlo, dhi, zb);
+        slot_max(p.peak + t, make_key(M * inv, (uint32_t)sb), atan2f(zb.y, zb.x), p.err);
     }
 }
 
