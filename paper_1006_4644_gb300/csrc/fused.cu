@@ -613,9 +613,11 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
 }
 
 // ------------------------------------------------------------ dispatch ----
+// Opt the kernel in to `bytes` of dynamic shared memory.  Always set: the
+// 48 KB default covers static plus dynamic memory, so a dynamic size below
+// 48 KB can still need the opt-in.
 template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes)
 {
-    if (bytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
