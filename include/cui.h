@@ -180,6 +180,23 @@ cui_status cui_cluster_triggers(cui_bank bank, cui_trigger *host_out, int64_t ca
 cui_status cui_trigger_chisq(cui_bank bank, int32_t bands, const cui_trigger *trig, int64_t n, float *host_chisq,
                              float *host_rho);
 
+/* The paper's own template form: the two polarisations of template `tmpl` in
+ * the time domain at the bank's sample rate, post-Newtonian order pn_x2 / 2
+ * (<= 2.5) in phase and Newtonian in amplitude (Sec. "template
+ * generation").  Orbital evolution in the TaylorT2 form from the binding
+ * energy and flux of circular orbits: t(v) and phi(v) as series in
+ * v = (M omega)^(1/3) (t_c = phi_c = 0); sample j is at
+ * t_j = -((N - j) mod N) / fs, so the chirp coalesces at sample 0 and runs
+ * backwards through the end of the buffer, as the SPA templates do.
+ * hp_dev[j] = v^2 cos 2 phi, hx_dev[j] = v^2 sin 2 phi between f_low and the
+ * innermost stable orbit (v = 6^-1/2), 0 elsewhere and for t < -N / fs.
+ * Device FP64 arrays of N samples, caller-owned.  Asynchronous.
+ * Uploaded as strain and filtered with the bank, it gives the match with the
+ * stationary-phase templates (the mismatch of eq:mismatch).
+ * Errors: CUI_ERR_ARG (template or order out of range, NULL pointers),
+ * CUI_ERR_CUDA. */
+cui_status cui_td_template(cui_bank bank, int64_t tmpl, int32_t pn_x2, double *hp_dev, double *hx_dev);
+
 /* sigma_t = sqrt(4 df sum_k |h~_k|^2 / S_k) of every template for the
  * uploaded PSD, to host_sigma[0 .. n_templates).  Synchronises.
  * Errors: CUI_ERR_STATE (no segment), CUI_ERR_CUDA.

@@ -141,6 +141,13 @@ class Bank:
                                              rho.ctypes.data), "cui_trigger_chisq")
         return chi, rho
 
+    def td_template(self, t: int, hp_dev, hx_dev, pn_x2: int = 5):
+        """Write the time-domain polarisations of template t (the paper's
+        generator form, TaylorT2, up to 2.5PN) into float64 device tensors of
+        N samples."""
+        _lib.check(self._l.cui_td_template(self._h, int(t), int(pn_x2), hp_dev.data_ptr(), hx_dev.data_ptr()),
+                   "cui_td_template")
+
     def sigma(self):
         out = np.zeros(self.n_templates)
         _lib.check(self._l.cui_bank_sigma(self._h, out.ctypes.data), "cui_bank_sigma")

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "td.h"
 
 using namespace cui;
 
@@ -189,7 +190,8 @@ struct cui_bank_s {
     int32_t *d_kex = nullptr;
     float2 *d_gexact = nullptr;
     std::vector<int32_t> h_kex;
-    std::vector<double> h_c0; // leading phase coefficient of every template
+    std::vector<double> h_c0;   // leading phase coefficient of every template
+    std::vector<double> h_mass; // (M in seconds, eta) of every template
     int kx = 0;
     void *d_y = nullptr;
     Slot *d_win = nullptr;
@@ -493,6 +495,7 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     chk(cudaMemcpyAsync(b->d_coef, coef.data(), sizeof(double) * nt * kNB, cudaMemcpyHostToDevice, s));
     chk(cudaMemcpyAsync(b->d_coef_df, coef_df.data(), sizeof(float2) * nt * kNB, cudaMemcpyHostToDevice, s));
     chk(cudaMemcpyAsync(b->d_mass, mass.data(), sizeof(double) * 2 * nt, cudaMemcpyHostToDevice, s));
+    b->h_mass = mass;
     chk(cudaMemcpyAsync(b->d_khi, b->h_khi.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
     chk(cudaMemcpyAsync(b->d_iota, iota.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
     chk(cudaMemsetAsync(b->d_peak, 0, sizeof(Slot) * nt, s));
@@ -1015,6 +1018,24 @@ extern "C" cui_status cui_trigger_chisq(cui_bank b, int32_t bands, const cui_tri
     cudaFree(d_trig);
     cudaFree(d_out);
     return st;
+}
+
+extern "C" cui_status cui_td_template(cui_bank b, int64_t t, int32_t pn_x2, double *hp_dev, double *hx_dev)
+{
+    if (!b || !hp_dev || !hx_dev) return fail(CUI_ERR_ARG, "bank and output pointers must be non-NULL");
+    if (t < 0 || t >= b->nt) return fail(CUI_ERR_ARG, "template %lld out of range", (long long)t);
+    if (pn_x2 < 0 || pn_x2 > 5) return fail(CUI_ERR_ARG, "the time-domain generator keeps up to 2.5PN (pn_x2 <= 5)");
+    TdArgs a;
+    td_coefficients(b->h_mass[2 * t], b->h_mass[2 * t + 1], pn_x2, a);
+    a.v_lo = std::cbrt(3.14159265358979323846 * a.M * b->desc.f_low);
+    a.v_hi = 1.0 / std::sqrt(6.0);
+    a.t_lo = td_time(a, a.v_lo);
+    a.t_hi = a.v_lo < a.v_hi ? td_time(a, a.v_hi) : a.t_lo - 1.0; // empty band: all zeros
+    a.fs = b->desc.sample_rate;
+    a.n = b->n;
+    CUI_TRY(launch_td_template(a, hp_dev, hx_dev, b->stream), "time-domain template");
+    launched();
+    return CUI_OK;
 }
 
 extern "C" cui_status cui_bank_sigma(cui_bank b, double *host_sigma)
