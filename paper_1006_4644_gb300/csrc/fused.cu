@@ -334,8 +334,12 @@ __global__ void __launch_bounds__(C *N1 / 16, p1_min_blocks(C *N1 / 16)) k_pass1
 }
 
 // ---------------------------------------------------------------- pass 2 ---
-// One spare slot every 16 keeps the stride-16 stores conflict-free.
-__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+// One spare slot every 16 keeps the stride-16 stores conflict-free.  Rows of
+// 4096 points add one more every 256: their last two stages run on half-warp
+// groups (below), whose stores step by 256 elements.
+template <int L> constexpr bool kGroupRows = L == 4096;
+template <int L> __device__ __forceinline__ int padi(int i) { return i + (i >> 4) + (kGroupRows<L> ? (i >> 8) : 0); }
+template <int L> constexpr int padded(int n) { return n + n / 16 + (kGroupRows<L> ? n / 256 : 0); }
 
 // Elements of pass 2 are one complex value (float2) or, in the paired layout,
 // the same position of two rows (c2, one row per lane).
@@ -352,16 +356,17 @@ __device__ __forceinline__ float2 lane(c2 z, int l) { return l ? make_float2(z.r
 template <int L, int R, int PPT, typename E> __device__ __forceinline__ void p2_load(E *v, const E *row, int lt)
 {
     constexpr int TPR = L / PPT, T = PPT / R, Q = L / R;
+    static_assert(!kGroupRows<L> || Q % 256 == 0, "padding step of the strided reads");
 #pragma unroll
     for (int i = 0; i < T; ++i) {
         const int j = lt + i * TPR;
         if constexpr (Q % 16 == 0) {
-            const E *b = row + padi(j);
+            const E *b = row + padi<L>(j);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[i * R + r] = b[r * (Q + Q / 16)];
+            for (int r = 0; r < R; ++r) v[i * R + r] = b[r * padded<L>(Q)];
         } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[i * R + r] = row[padi(j + r * Q)];
+            for (int r = 0; r < R; ++r) v[i * R + r] = row[padi<L>(j + r * Q)];
         }
     }
 }
@@ -371,21 +376,23 @@ template <int L, int R, int NS, int PPT, typename E>
 __device__ __forceinline__ void p2_store(const E *v, E *row, int lt)
 {
     constexpr int TPR = L / PPT, T = PPT / R;
+    // a thread's R outputs stay inside one block of 256 elements
+    static_assert(!kGroupRows<L> || NS * R <= 256, "padding step of the strided writes");
 #pragma unroll
     for (int i = 0; i < T; ++i) {
         const int j = lt + i * TPR;
         const int idx = (j / NS) * NS * R + (j & (NS - 1));
         if constexpr (NS % 16 == 0) {
-            E *b = row + padi(idx);
+            E *b = row + padi<L>(idx);
 #pragma unroll
             for (int r = 0; r < R; ++r) b[r * (NS + NS / 16)] = v[i * R + r];
         } else if constexpr (NS == 1) {
-            E *b = row + padi(idx); // idx = R j and (R j mod 16) + r < 16
+            E *b = row + padi<L>(idx); // idx = R j and (R j mod 16) + r < 16
 #pragma unroll
             for (int r = 0; r < R; ++r) b[r] = v[i * R + r];
         } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) row[padi(idx + r * NS)] = v[i * R + r];
+            for (int r = 0; r < R; ++r) row[padi<L>(idx + r * NS)] = v[i * R + r];
         }
     }
 }
@@ -490,7 +497,7 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
     constexpr int NL = lanes_of<E>;
     constexpr int TPR = L / PPT;
     constexpr int NT = RPC * TPR;
-    constexpr int LP = L + L / 16;
+    constexpr int LP = padded<L>(L);
     constexpr int NW = NT / 32;
     constexpr int RL = R3 > 1 ? R3 : (R2 > 1 ? R2 : R1);
     constexpr int NSL = L / RL;
@@ -502,6 +509,13 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
     __shared__ float s_max[NW];
     const int tid = threadIdx.x;
     const int rr = tid / TPR, lt = tid % TPR;
+    // Rows of 16 x 16 x 16 points: after stage 0 the row splits into 16
+    // independent 256-point transforms, sub-transform g touching only the
+    // positions = g (mod 16).  Thread lt = 16 g + q takes task j = 16 q + g of
+    // the last two stages, so each sub-transform lives in one half-warp and
+    // those stages exchange through shared memory under warp barriers only.
+    constexpr bool GROUP = kGroupRows<L> && R0 == 16 && R1 == 16 && R2 == 16 && R3 == 1 && PPT == 16;
+    const int lg = GROUP ? (lt & 15) * 16 + (lt >> 4) : lt;
     const int y = blockIdx.y;
     const int t = p.order[p.base + y];
     const int c = blockIdx.x * RPC + rr;
@@ -534,7 +548,12 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
         for (int m = tid; m < LINES; m += NT)
             asm volatile("discard.global.L2 [%0], 128;" ::"l"(yb + (size_t)m * 128) : "memory");
     }
-    if constexpr (R2 > 1) {
+    if constexpr (GROUP) {
+        p2_stage<L, R1, R0, true, PPT>(v, row, lg, tw1);
+        __syncwarp();
+        p2_store<L, R1, R0, PPT>(v, row, lg);
+        __syncwarp();
+    } else if constexpr (R2 > 1) {
         p2_stage<L, R1, R0, true, PPT>(v, row, lt, tw1);
         __syncthreads();
         p2_store<L, R1, R0, PPT>(v, row, lt);
@@ -546,7 +565,7 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
             __syncthreads();
         }
     }
-    p2_stage<L, RL, NSL, R2 == 1, PPT>(v, row, lt, tw1);
+    p2_stage<L, RL, NSL, R2 == 1, PPT>(v, row, lg, tw1);
 
     // Epilogue.  Output d of lane l is sample s = c_l + n1 d with
     // c_l = c + l n1/2; |z|^2 is compared before the (positive) scaling.  The
@@ -571,8 +590,8 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
         }
         m[l] = -1.f;
     }
-    if (full) p2_max<L, RL, false, PPT>(v, lt, m, dlo, dhi);
-    else p2_max<L, RL, true, PPT>(v, lt, m, dlo, dhi);
+    if (full) p2_max<L, RL, false, PPT>(v, lg, m, dlo, dhi);
+    else p2_max<L, RL, true, PPT>(v, lg, m, dlo, dhi);
 
     float mx = m[0];
 #pragma unroll
@@ -584,7 +603,7 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
         for (int r = 0; r < RL; ++r)
 #pragma unroll
             for (int i = 0; i < TL; ++i) {
-                const int d = lt + i * TPR + r * (L / RL);
+                const int d = lg + i * TPR + r * (L / RL);
                 const float2 a = abs2(v[i * RL + r]);
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
@@ -607,7 +626,7 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
     for (int w = 1; w < NW; ++w) M = fmaxf(M, s_max[w]);
     if (M >= 0.f && mx == M) {
         float2 zb = make_float2(0.f, 0.f);
-        const int64_t sb = p2_find<L, RL, PPT>(v, lt, M, cl, n1, dlo, dhi, zb);
+        const int64_t sb = p2_find<L, RL, PPT>(v, lg, M, cl, n1, dlo, dhi, zb);
         slot_max(p.peak + t, make_key(M * inv, (uint32_t)sb), atan2f(zb.y, zb.x), p.err);
     }
 }
@@ -629,7 +648,8 @@ static bool paired(int n2) { return n2 <= kPairMaxL; }
 size_t fused_pass1_smem(int n1, int ccols) { return (size_t)n1 * ccols * sizeof(float2); }
 size_t fused_pass2_smem(int n2, int rpc)
 {
-    return (size_t)rpc * (n2 + n2 / 16) * (paired(n2) ? sizeof(c2) : sizeof(float2));
+    const int lp = n2 + n2 / 16 + (n2 == 4096 ? n2 / 256 : 0); // padded<L> of the kernel
+    return (size_t)rpc * lp * (paired(n2) ? sizeof(c2) : sizeof(float2));
 }
 
 bool fused_supported(int log2n) { return log2n >= 12 && log2n <= 22; }
