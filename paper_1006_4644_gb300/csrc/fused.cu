@@ -335,11 +335,17 @@ __global__ void __launch_bounds__(C *N1 / 16, p1_min_blocks(C *N1 / 16)) k_pass1
 
 // ---------------------------------------------------------------- pass 2 ---
 // One spare slot every 16 keeps the stride-16 stores conflict-free.  Rows of
-// 4096 points add one more every 256: their last two stages run on half-warp
-// groups (below), whose stores step by 256 elements.
-template <int L> constexpr bool kGroupRows = L == 4096;
-template <int L> __device__ __forceinline__ int padi(int i) { return i + (i >> 4) + (kGroupRows<L> ? (i >> 8) : 0); }
-template <int L> constexpr int padded(int n) { return n + n / 16 + (kGroupRows<L> ? n / 256 : 0); }
+// 4096 and 16384 points run their last two stages on half-warp groups (see
+// k_pass2), whose accesses step by 256 or 1024 elements; extra slots every
+// 256 (and 4096) keep those conflict-free too.  For a power of two Q and
+// 0 <= j < Q, padi(j + r Q) = padi(j) + padi(r Q): the strided accesses below
+// add a compile-time offset to one computed base.
+template <int L> constexpr bool kGroupRows = L == 4096 || L == 16384;
+template <int L> __host__ __device__ constexpr int padi(int i)
+{
+    return i + (i >> 4) + (kGroupRows<L> ? (i >> 8) : 0) + (L == 16384 ? (i >> 12) : 0);
+}
+template <int L> constexpr int padded() { return kGroupRows<L> ? padi<L>(L - 1) + 1 : L + L / 16; }
 
 // Elements of pass 2 are one complex value (float2) or, in the paired layout,
 // the same position of two rows (c2, one row per lane).
@@ -356,18 +362,11 @@ __device__ __forceinline__ float2 lane(c2 z, int l) { return l ? make_float2(z.r
 template <int L, int R, int PPT, typename E> __device__ __forceinline__ void p2_load(E *v, const E *row, int lt)
 {
     constexpr int TPR = L / PPT, T = PPT / R, Q = L / R;
-    static_assert(!kGroupRows<L> || Q % 256 == 0, "padding step of the strided reads");
 #pragma unroll
     for (int i = 0; i < T; ++i) {
-        const int j = lt + i * TPR;
-        if constexpr (Q % 16 == 0) {
-            const E *b = row + padi<L>(j);
+        const E *b = row + padi<L>(lt + i * TPR); // task j = lt + i L/PPT < Q
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[i * R + r] = b[r * padded<L>(Q)];
-        } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[i * R + r] = row[padi<L>(j + r * Q)];
-        }
+        for (int r = 0; r < R; ++r) v[i * R + r] = b[padi<L>(r * Q)];
     }
 }
 
@@ -376,24 +375,13 @@ template <int L, int R, int NS, int PPT, typename E>
 __device__ __forceinline__ void p2_store(const E *v, E *row, int lt)
 {
     constexpr int TPR = L / PPT, T = PPT / R;
-    // a thread's R outputs stay inside one block of 256 elements
-    static_assert(!kGroupRows<L> || NS * R <= 256, "padding step of the strided writes");
 #pragma unroll
     for (int i = 0; i < T; ++i) {
         const int j = lt + i * TPR;
-        const int idx = (j / NS) * NS * R + (j & (NS - 1));
-        if constexpr (NS % 16 == 0) {
-            E *b = row + padi<L>(idx);
+        // idx is a multiple of NS R plus j mod NS < NS, so the padding splits as above
+        E *b = row + padi<L>((j / NS) * NS * R + (j & (NS - 1)));
 #pragma unroll
-            for (int r = 0; r < R; ++r) b[r * (NS + NS / 16)] = v[i * R + r];
-        } else if constexpr (NS == 1) {
-            E *b = row + padi<L>(idx); // idx = R j and (R j mod 16) + r < 16
-#pragma unroll
-            for (int r = 0; r < R; ++r) b[r] = v[i * R + r];
-        } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r) row[padi<L>(idx + r * NS)] = v[i * R + r];
-        }
+        for (int r = 0; r < R; ++r) b[padi<L>(r * NS)] = v[i * R + r];
     }
 }
 
@@ -497,7 +485,7 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
     constexpr int NL = lanes_of<E>;
     constexpr int TPR = L / PPT;
     constexpr int NT = RPC * TPR;
-    constexpr int LP = padded<L>(L);
+    constexpr int LP = padded<L>();
     constexpr int NW = NT / 32;
     constexpr int RL = R3 > 1 ? R3 : (R2 > 1 ? R2 : R1);
     constexpr int NSL = L / RL;
@@ -509,13 +497,13 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
     __shared__ float s_max[NW];
     const int tid = threadIdx.x;
     const int rr = tid / TPR, lt = tid % TPR;
-    // Rows of 16 x 16 x 16 points: after stage 0 the row splits into 16
-    // independent 256-point transforms, sub-transform g touching only the
-    // positions = g (mod 16).  Thread lt = 16 g + q takes task j = 16 q + g of
-    // the last two stages, so each sub-transform lives in one half-warp and
-    // those stages exchange through shared memory under warp barriers only.
-    constexpr bool GROUP = kGroupRows<L> && R0 == 16 && R1 == 16 && R2 == 16 && R3 == 1 && PPT == 16;
-    const int lg = GROUP ? (lt & 15) * 16 + (lt >> 4) : lt;
+    // When the last two radices are 16, the row splits before them into
+    // G = L / 256 independent 256-point transforms, transform g touching only
+    // the positions = g (mod G).  Thread lt = 16 g + q takes task j = G q + g
+    // of those two stages, so each transform lives in one half-warp and the
+    // exchange between them needs warp barriers only.
+    constexpr bool GROUP = kGroupRows<L> && PPT == 16 && RL == 16 && (R3 > 1 ? R2 : R1) == 16;
+    const int lg = GROUP ? (lt & 15) * (L / 256) + (lt >> 4) : lt;
     const int y = blockIdx.y;
     const int t = p.order[p.base + y];
     const int c = blockIdx.x * RPC + rr;
@@ -548,7 +536,7 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
         for (int m = tid; m < LINES; m += NT)
             asm volatile("discard.global.L2 [%0], 128;" ::"l"(yb + (size_t)m * 128) : "memory");
     }
-    if constexpr (GROUP) {
+    if constexpr (GROUP && R3 == 1) {
         p2_stage<L, R1, R0, true, PPT>(v, row, lg, tw1);
         __syncwarp();
         p2_store<L, R1, R0, PPT>(v, row, lg);
@@ -558,7 +546,12 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
         __syncthreads();
         p2_store<L, R1, R0, PPT>(v, row, lt);
         __syncthreads();
-        if constexpr (R3 > 1) {
+        if constexpr (R3 > 1 && GROUP) {
+            p2_stage<L, R2, R0 * R1, true, PPT>(v, row, lg, tw2);
+            __syncwarp();
+            p2_store<L, R2, R0 * R1, PPT>(v, row, lg);
+            __syncwarp();
+        } else if constexpr (R3 > 1) {
             p2_stage<L, R2, R0 * R1, true, PPT>(v, row, lt, tw2);
             __syncthreads();
             p2_store<L, R2, R0 * R1, PPT>(v, row, lt);
@@ -648,7 +641,9 @@ static bool paired(int n2) { return n2 <= kPairMaxL; }
 size_t fused_pass1_smem(int n1, int ccols) { return (size_t)n1 * ccols * sizeof(float2); }
 size_t fused_pass2_smem(int n2, int rpc)
 {
-    const int lp = n2 + n2 / 16 + (n2 == 4096 ? n2 / 256 : 0); // padded<L> of the kernel
+    int lp = n2 + n2 / 16; // padded<L>() of the kernel
+    if (n2 == 4096) lp = padded<4096>();
+    if (n2 == 16384) lp = padded<16384>();
     return (size_t)rpc * lp * (paired(n2) ? sizeof(c2) : sizeof(float2));
 }
 
