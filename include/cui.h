@@ -180,6 +180,59 @@ cui_status cui_cluster_triggers(cui_bank bank, cui_trigger *host_out, int64_t ca
 cui_status cui_trigger_chisq(cui_bank bank, int32_t bands, const cui_trigger *trig, int64_t n, float *host_chisq,
                              float *host_rho);
 
+/* Multi-band search (Sec. "Online analysis considerations": the frequency
+ * range divided into bands, the matched filter run first on the upper band,
+ * where the chirp is shortest and carries most of the SNR, and the lower bands
+ * added afterwards for the candidates).
+ *
+ * cui_bank_set_band restricts every later filter call, and the sigma, chi^2
+ * and clustering results that follow from it, to each template's bins in
+ * [f_lo, f_hi): bins k_lo' <= k < min(k_hi(t), k_hi') with
+ * k_lo' = max(k_low, ceil(f_lo / df)) and k_hi' = ceil(f_hi / df), capped at
+ * N/2; f_hi <= 0 sets no upper limit, and f_lo <= f_low with f_hi <= 0 gives
+ * back the full band.  sigma^2 is the template's power inside the band, so rho
+ * is the band's own SNR.  With f_lo well above f_low the band's chirp lasts
+ * only tau(f_lo), and the band can be searched on segments much shorter than
+ * the whole template.  The band stays in force across uploads until it is set
+ * again.  Asynchronous; the host waits once, for earlier calls on the stream.
+ * Errors: CUI_ERR_ARG (NULL bank, edges not finite), CUI_ERR_CUDA. */
+cui_status cui_bank_set_band(cui_bank bank, double f_lo, double f_hi);
+
+/* Band correlators at arbitrary times, by direct sums over the band's bins (no
+ * FFT).  Query i is template tmpl[i] at time t_sec[i] (seconds after the
+ * segment's first sample, taken modulo T = N / fs):
+ *   z_i = 4 df sum_{k in B_i} d~_k conj(h~_k) / S_k exp(+2 pi i k df t_i),
+ *   sigma_i^2 = 4 df sum_{k in B_i} |h~_k|^2 / S_k,
+ * h~_k = f_k^(-7/6) exp(-i Psi(f_k)) generated exactly as the filter generates
+ * it, B_i = [max(f_lo, f_low), f_hi) cut to the template's own band [f_low,
+ * f_isco) (f_hi <= 0: no upper limit), whatever cui_bank_set_band holds.  At a
+ * sample time j / fs over the filter's band, z_i / sigma is the filter's rho
+ * with its phase.  Both are in physical units (strain and PSD as uploaded,
+ * frequencies in Hz), so that the results of banks holding the same data at
+ * other lengths or sample rates add up: over disjoint bands b of one template
+ * at one time, rho = |sum_b z_b| / sqrt(sum_b sigma_b^2).  host_z receives 2n
+ * doubles (Re z_i, Im z_i), host_sigma2 (nullable) n doubles.  Fused banks
+ * only.  Synchronises.  Errors: CUI_ERR_ARG (template out of range, time or
+ * edges not finite, NULL pointers), CUI_ERR_STATE (plain bank, no segment),
+ * CUI_ERR_CUDA, CUI_ERR_TIMEOUT. */
+cui_status cui_band_correlate(cui_bank bank, const int32_t *tmpl, const double *t_sec, int64_t n, double f_lo,
+                              double f_hi, double *host_z, double *host_sigma2);
+
+/* The uploaded segment restricted to one band and resampled, for the
+ * multi-band search: the series that the upper band is searched on (short
+ * segments cut from it, at the full rate) and the decimated series that
+ * carries a lower band to a bank at a lower sample rate.
+ *   x'_j = (1/N) sum_{k in B} X_k e^(+2 pi i k j / m) + c.c., j < m = N / decim,
+ * X_k = sum_j d_j e^(-2 pi i jk/N) the segment's DFT (computed at upload in
+ * double-float, near-FP64 accuracy) and B the bins ceil(f_lo/df) <= k <
+ * ceil(f_hi/df) below m/2 (f_hi <= 0: up to m/2; the bin at m/2 is dropped).
+ * With decim = 1 it is the band-passed segment at the full rate; a band below
+ * the new Nyquist frequency fs / (2 decim) loses nothing by the decimation.
+ * out_dev: m doubles of device memory, caller-owned.  decim: a power of two,
+ * N / decim >= 16.  Asynchronous on the bank's stream.  Errors: CUI_ERR_ARG,
+ * CUI_ERR_STATE (no segment), CUI_ERR_CUDA. */
+cui_status cui_segment_band_series(cui_bank bank, double f_lo, double f_hi, int32_t decim, double *out_dev);
+
 /* The paper's own template form: the two polarisations of template `tmpl` in
  * the time domain at the bank's sample rate, post-Newtonian order pn_x2 / 2
  * (<= 2.5) in phase and Newtonian in amplitude (Sec. "template

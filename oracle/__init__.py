@@ -24,6 +24,11 @@ Each function names the part of the paper it follows:
 * ``chisq``            -- the chi-squared signal-consistency test that the
   paper lists as future work (Sec. "Conclusions"), in its equal-power
   sub-band form: chi^2 = p sum_l |z_l - z/p|^2 / sigma^2
+* ``band_edges`` / ``band_filter_template`` / ``band_correlate`` /
+  ``band_series`` -- the multi-band search of Sec. "Online analysis
+  considerations" (the band split, the filter restricted to one band, the band
+  correlators summed directly at any time, which add up across bands and
+  segments, and the data restricted to a band and resampled)
 * ``fft`` / ``dft``    -- textbook radix-2 FFT and naive DFT used above
 
 Parity unpinned: the absolute constant of Psi (-pi/4 and the constant part of
@@ -274,3 +279,66 @@ def chisq(dtilde, psd, m1: float, m2: float, pn_x2: int, f_low: float, fs: float
         chi.append(bands * np.sum(np.abs(zl - z / bands) ** 2) / s2)
         rho.append(abs(z) / np.sqrt(s2))
     return np.array(chi), np.array(rho)
+
+
+def band_edges(m1: float, m2: float, f_low: float, fs: float, n: int, f_lo: float, f_hi: float):
+    """[k_a, k_b) of a template cut to the band [f_lo, f_hi): the template's own
+    band [k_lo, k_hi) intersected with ceil(f_lo/df) <= k < ceil(f_hi/df)
+    (f_hi <= 0: no upper limit); an empty band has k_a == k_b."""
+    k_lo, k_hi = template_band(m1, m2, f_low, fs, n)
+    df = fs / n
+    ka = max(k_lo, int(np.ceil(f_lo / df)))
+    kb = k_hi if f_hi <= 0 else min(k_hi, int(np.ceil(f_hi / df)))
+    return ka, max(ka, kb)
+
+
+def band_filter_template(dtilde, psd, m1: float, m2: float, pn_x2: int, f_low: float, fs: float, n: int,
+                         f_lo: float, f_hi: float, lo: int = 0, hi: int | None = None, window: int | None = None,
+                         thr: float = 6.0, cap: int = 1 << 16):
+    """The per-chunk loop of one template with the template restricted to the
+    band [f_lo, f_hi): z_j by the FFT route over the band's bins only, sigma^2
+    over the same bins, then the peak and the triggers of rho = |z| / sigma."""
+    hi = n if hi is None else hi
+    window = int(fs) if window is None else window
+    h, _, _ = spa_template(m1, m2, pn_x2, f_low, fs, n)
+    ka, kb = band_edges(m1, m2, f_low, fs, n, f_lo, f_hi)
+    s2 = sigma2(h, psd, fs, n, ka, kb)
+    z = correlate(dtilde, h, psd, fs, n, ka, kb)
+    out = peak_triggers(z, s2 if s2 > 0 else 1.0, lo, hi, window, thr, cap)
+    out["sigma2"] = s2
+    return out
+
+
+def band_correlate(dtilde, psd, m1: float, m2: float, pn_x2: int, f_low: float, fs: float, n: int, times,
+                   f_lo: float, f_hi: float):
+    """(z, sigma^2) of one template over the band [f_lo, f_hi) at arbitrary
+    times t (seconds after the segment's first sample), by direct summation:
+    z(t) = 4 df sum_{k in band} d~_k conj(h~_k) / S_k exp(2 pi i k df t) and
+    sigma^2 = 4 df sum |h~_k|^2 / S_k, in physical units."""
+    h, _, _ = spa_template(m1, m2, pn_x2, f_low, fs, n)
+    ka, kb = band_edges(m1, m2, f_low, fs, n, f_lo, f_hi)
+    psd = _f64(psd)
+    df = fs / n
+    k = np.arange(ka, kb)
+    terms = 4.0 * df * np.asarray(dtilde)[ka:kb] * np.conj(h[ka:kb]) / psd[ka:kb]
+    s2 = float(4.0 * df * np.sum(np.abs(h[ka:kb]) ** 2 / psd[ka:kb]))
+    z = np.empty(len(times), dtype=np.complex128)
+    for i, t in enumerate(times):
+        x = (float(t) * df) % 1.0  # t / T mod 1
+        z[i] = np.sum(terms * np.exp(2j * np.pi * ((k * x) % 1.0)))
+    return z, s2
+
+
+def band_series(strain, fs: float, f_lo: float, f_hi: float, decim: int):
+    """The segment restricted to the bins ceil(f_lo/df) <= k < ceil(f_hi/df)
+    below m/2 (f_hi <= 0: up to m/2) at the sample rate fs/decim, m = n/decim:
+    x'_j = (1/n) sum_{k in band} X_k e^{2 pi i k j / m} + c.c., X the DFT."""
+    n = len(strain)
+    m = n // decim
+    df = fs / n
+    X = segment_spectrum(strain, fs) * fs  # sum_j d_j e^{-2 pi i jk/n}
+    k = np.arange(m // 2 + 1)
+    ka = max(0, int(np.ceil(f_lo / df)))
+    kb = m // 2 if f_hi <= 0 else min(m // 2, int(np.ceil(f_hi / df)))
+    Y = np.where((k >= ka) & (k < kb), X[: m // 2 + 1], 0.0)
+    return np.fft.irfft(Y, m) * (m / n)

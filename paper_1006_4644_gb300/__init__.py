@@ -141,6 +141,34 @@ class Bank:
                                              rho.ctypes.data), "cui_trigger_chisq")
         return chi, rho
 
+    def set_band(self, f_lo: float = 0.0, f_hi: float = 0.0):
+        """Restrict later filter calls to each template's bins in [f_lo, f_hi)
+        (f_hi <= 0: no upper limit; set_band() restores the full band)."""
+        _lib.check(self._l.cui_bank_set_band(self._h, float(f_lo), float(f_hi)), "cui_bank_set_band")
+
+    def band_correlate(self, tmpl, t_sec, f_lo: float = 0.0, f_hi: float = 0.0):
+        """(z, sigma^2) of templates tmpl[i] at times t_sec[i] (seconds after the
+        segment's first sample) over the band [f_lo, f_hi), by direct sums, in
+        physical units: complex128 z and float64 sigma^2 arrays."""
+        tm = np.ascontiguousarray(tmpl, dtype=np.int32)
+        ts = np.ascontiguousarray(t_sec, dtype=np.float64)
+        if tm.shape != ts.shape:
+            raise ValueError("tmpl and t_sec must have the same length")
+        z = np.zeros(2 * len(tm))
+        s2 = np.zeros(len(tm))
+        _lib.check(self._l.cui_band_correlate(self._h, tm.ctypes.data, ts.ctypes.data, len(tm), float(f_lo),
+                                              float(f_hi), z.ctypes.data, s2.ctypes.data), "cui_band_correlate")
+        return z[0::2] + 1j * z[1::2], s2
+
+    def band_series(self, out_dev, f_lo: float = 0.0, f_hi: float = 0.0, decim: int = 1):
+        """Write the uploaded segment restricted to [f_lo, f_hi) at the sample
+        rate fs / decim into a float64 device tensor of N / decim samples."""
+        if out_dev.numel() != self.n // max(1, int(decim)) or str(out_dev.dtype) != "torch.float64" \
+                or not out_dev.is_contiguous():
+            raise ValueError("out_dev must be a contiguous float64 device tensor of N / decim samples")
+        _lib.check(self._l.cui_segment_band_series(self._h, float(f_lo), float(f_hi), int(decim), out_dev.data_ptr()),
+                   "cui_segment_band_series")
+
     def td_template(self, t: int, hp_dev, hx_dev, pn_x2: int = 5):
         """Write the time-domain polarisations of template t (the paper's
         generator form, TaylorT2, up to 2.5PN) into float64 device tensors of

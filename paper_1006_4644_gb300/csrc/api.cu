@@ -161,11 +161,14 @@ struct cui_bank_s {
     int log2n = 0;
     int64_t n = 0, nh = 0, nt = 0;
     int k_low = 0;
+    int band_lo = 0, band_hi = 0; // band of the filter calls: [band_lo, min(band_hi, k_hi(t)))
     double df = 0;
     bool fused = false, plain_fp64 = false;
     int nwin = 0;
     // per template
-    std::vector<int32_t> h_khi;
+    std::vector<int32_t> h_khi;     // k_hi(t): first bin at or above f_isco, capped at N/2
+    std::vector<int32_t> h_khi_eff; // min(k_hi(t), band_hi), the copy behind d_khi
+    int32_t *d_khi0 = nullptr;      // k_hi(t)
     double *d_coef = nullptr;
     float2 *d_coef_df = nullptr;
     double *d_mass = nullptr;
@@ -290,7 +293,7 @@ struct Span {
 
 static void release(cui_bank b)
 {
-    void *ptrs[] = {b->d_coef, b->d_coef_df, b->d_mass, b->d_khi, b->d_sigma2, b->d_invnorm, b->d_peak, b->d_peaks,
+    void *ptrs[] = {b->d_coef, b->d_coef_df, b->d_mass, b->d_khi, b->d_khi0, b->d_sigma2, b->d_invnorm, b->d_peak, b->d_peaks,
                     b->d_iota, b->d_strain, b->d_psd, b->d_amp, b->d_prefix, b->d_scan, b->d_fa, b->d_fb,
                     b->tw.lo64, b->tw.hi64, b->tw.lo32, b->tw.hi32, b->tw.lodf, b->tw.hidf,
                     b->d_wbar, b->d_dS, b->d_scales, b->d_basis, b->d_basis_df, b->d_kex, b->d_gexact, b->d_y,
@@ -409,6 +412,8 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     b->nt = n_templates;
     b->df = d.sample_rate / (double)d.n;
     b->k_low = std::max<int>(1, (int)std::ceil(d.f_low / b->df));
+    b->band_lo = b->k_low;
+    b->band_hi = (int)(d.n / 2);
     b->fused = !(d.flags & CUI_PLAIN) && fused_supported(b->log2n);
     b->plain_fp64 = (d.flags & CUI_PLAIN) && (d.flags & CUI_PLAIN_FP64);
     b->nwin = (int)((d.valid_hi - d.valid_lo + d.window - 1) / d.window);
@@ -446,6 +451,7 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     chk(dalloc(&b->d_coef_df, nt * kNB));
     chk(dalloc(&b->d_mass, 2 * nt));
     chk(dalloc(&b->d_khi, nt));
+    chk(dalloc(&b->d_khi0, nt));
     chk(dalloc(&b->d_sigma2, nt));
     chk(dalloc(&b->d_invnorm, nt));
     chk(dalloc(&b->d_peak, nt));
@@ -497,6 +503,8 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     chk(cudaMemcpyAsync(b->d_mass, mass.data(), sizeof(double) * 2 * nt, cudaMemcpyHostToDevice, s));
     b->h_mass = mass;
     chk(cudaMemcpyAsync(b->d_khi, b->h_khi.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(b->d_khi0, b->h_khi.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
+    b->h_khi_eff = b->h_khi;
     chk(cudaMemcpyAsync(b->d_iota, iota.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
     chk(cudaMemsetAsync(b->d_peak, 0, sizeof(Slot) * nt, s));
     chk(cudaMemsetAsync(b->d_err, 0, sizeof(int), s));
@@ -586,8 +594,8 @@ extern "C" cui_status cui_segment_upload(cui_bank b, const double *strain, int64
     launch_weighted_data(X, b->d_psd, b->d_amp, b->n, b->k_low, b->desc.sample_rate, b->d_scales, b->d_wbar,
                          b->d_dS, b->plain_fp64, s);
     launch_prefix(b->d_psd, b->d_amp, b->n, b->k_low, b->d_prefix, b->d_scan, s);
-    launch_template_norm(b->d_prefix, b->d_khi, b->nt, b->desc.sample_rate, b->n, b->d_scales, b->d_sigma2,
-                         b->d_invnorm, s);
+    launch_template_norm(b->d_prefix, b->d_khi, b->band_lo, b->nt, b->desc.sample_rate, b->n, b->d_scales,
+                         b->d_sigma2, b->d_invnorm, s);
     CUI_TRY(cudaGetLastError(), "cui_segment_upload");
     b->have_segment = true;
     b->filtered = false;
@@ -606,6 +614,7 @@ static FusedArgs fused_args(cui_bank b, const int32_t *order, int64_t base)
     a.kex = b->d_kex;
     a.gexact = b->d_gexact;
     a.invnorm = b->d_invnorm;
+    a.k_low = b->band_lo;
     a.order = order;
     a.base = base;
     a.ywork = b->d_y;
@@ -618,7 +627,6 @@ static FusedArgs fused_args(cui_bank b, const int32_t *order, int64_t base)
     a.n2 = b->n2;
     a.ccols = b->ccols;
     a.rpc = b->rpc;
-    a.k_low = b->k_low;
     a.lo = b->desc.valid_lo;
     a.hi = b->desc.valid_hi;
     a.window = b->desc.window;
@@ -764,7 +772,7 @@ extern "C" cui_status cui_filter_bank(cui_bank b, const int32_t *order, int64_t 
         a.n = b->n;
         a.log2n = b->log2n;
         a.pn_x2 = b->desc.pn_order_x2;
-        a.k_low = b->k_low;
+        a.k_low = b->band_lo;
         a.fs = b->desc.sample_rate;
         a.lo = b->desc.valid_lo;
         a.hi = b->desc.valid_hi;
@@ -1018,6 +1026,110 @@ extern "C" cui_status cui_trigger_chisq(cui_bank b, int32_t bands, const cui_tri
     cudaFree(d_trig);
     cudaFree(d_out);
     return st;
+}
+
+extern "C" cui_status cui_bank_set_band(cui_bank b, double f_lo, double f_hi)
+{
+    if (!b) return fail(CUI_ERR_ARG, "bank is NULL");
+    if (!std::isfinite(f_lo) || !std::isfinite(f_hi)) return fail(CUI_ERR_ARG, "band edges must be finite");
+    const double klo = std::ceil(f_lo / b->df), khi = std::ceil(f_hi / b->df);
+    const int lo = (int)std::max<double>(b->k_low, std::min<double>(klo, (double)b->nh));
+    const int hi = f_hi <= 0.0 ? (int)b->nh : (int)std::max<double>(lo, std::min<double>(khi, (double)b->nh));
+    if (lo == b->band_lo && hi == b->band_hi) return CUI_OK;
+    const cudaStream_t s = b->stream;
+    // the pageable copy source below is reused: wait for any earlier copy of it
+    CUI_TRY(cudaStreamSynchronize(s), "stream synchronize");
+    b->band_lo = lo;
+    b->band_hi = hi;
+    for (int64_t t = 0; t < b->nt; ++t) b->h_khi_eff[t] = std::min<int32_t>(b->h_khi[t], hi);
+    CUI_TRY(cudaMemcpyAsync(b->d_khi, b->h_khi_eff.data(), sizeof(int32_t) * b->nt, cudaMemcpyHostToDevice, s),
+            "band copy");
+    if (b->gexec) { // the captured call holds the old lower edge
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    if (b->have_segment)
+        launch_template_norm(b->d_prefix, b->d_khi, b->band_lo, b->nt, b->desc.sample_rate, b->n, b->d_scales,
+                             b->d_sigma2, b->d_invnorm, s);
+    b->filtered = false;
+    CUI_TRY(cudaGetLastError(), "cui_bank_set_band");
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_segment_band_series(cui_bank b, double f_lo, double f_hi, int32_t decim, double *out_dev)
+{
+    if (!b || !out_dev) return fail(CUI_ERR_ARG, "bank and out_dev must be non-NULL");
+    if (!std::isfinite(f_lo) || !std::isfinite(f_hi)) return fail(CUI_ERR_ARG, "band edges must be finite");
+    if (decim < 1 || (decim & (decim - 1)) || (int64_t)decim > b->n / 16)
+        return fail(CUI_ERR_ARG, "decim must be a power of two with N / decim >= 16");
+    if (!b->have_segment || !b->d_X) return fail(CUI_ERR_STATE, "no segment uploaded");
+    const int64_t m = b->n / decim;
+    const double klo = std::ceil(f_lo / b->df), khi = std::ceil(f_hi / b->df);
+    const int64_t ka = (int64_t)std::max<double>(0.0, std::min<double>(klo, (double)(m / 2)));
+    const int64_t kb = f_hi <= 0.0 ? m / 2 : (int64_t)std::max<double>(ka, std::min<double>(khi, (double)(m / 2)));
+    const cudaStream_t s = b->stream;
+    dfc *a = nullptr;
+    CUI_TRY(cudaMallocAsync(&a, sizeof(dfc) * 2 * m, s), "band series buffers");
+    launch_band_series(b->d_X, b->n, ilog2(m), ka, kb, b->tw, a, a + m, out_dev, s);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(a, s);
+    CUI_TRY(e, "cui_segment_band_series");
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_band_correlate(cui_bank b, const int32_t *tmpl, const double *t_sec, int64_t n,
+                                         double f_lo, double f_hi, double *host_z, double *host_sigma2)
+{
+    if (!b) return fail(CUI_ERR_ARG, "bank is NULL");
+    if (n < 0 || n > (int64_t(1) << 30) || (n > 0 && (!tmpl || !t_sec || !host_z)))
+        return fail(CUI_ERR_ARG, "bad query count or NULL pointers");
+    if (!std::isfinite(f_lo) || !std::isfinite(f_hi)) return fail(CUI_ERR_ARG, "band edges must be finite");
+    if (!b->fused) return fail(CUI_ERR_STATE, "band sums need the fused path (N >= 2^12, no CUI_PLAIN)");
+    if (!b->have_segment) return fail(CUI_ERR_STATE, "no segment uploaded");
+    if (n == 0) return CUI_OK;
+    const double T = (double)b->n / b->desc.sample_rate;
+    std::vector<int32_t> ht(n);
+    std::vector<uint64_t> hu(n);
+    for (int64_t i = 0; i < n; ++i) {
+        if (tmpl[i] < 0 || tmpl[i] >= b->nt) return fail(CUI_ERR_ARG, "query %lld: template out of range", (long long)i);
+        if (!std::isfinite(t_sec[i])) return fail(CUI_ERR_ARG, "query %lld: time must be finite", (long long)i);
+        ht[i] = tmpl[i];
+        // t / T mod 1 as a 64-bit fraction (exact for sample times j / fs)
+        double fr = t_sec[i] / T;
+        fr -= std::floor(fr);
+        const double x = std::ldexp(fr, 64);
+        hu[i] = x >= 18446744073709551616.0 ? 0ull : (uint64_t)x;
+    }
+    const double klo = std::ceil(f_lo / b->df), khi = std::ceil(f_hi / b->df);
+    const int ka = (int)std::max<double>(b->k_low, std::min<double>(klo, (double)b->nh));
+    const int kb = f_hi <= 0.0 ? (int)b->nh : (int)std::max<double>(ka, std::min<double>(khi, (double)b->nh));
+    const double df = b->df;
+    const double zfac = 4.0 * df * std::pow(df, -7.0 / 6.0), sfac = 4.0 * df * std::pow(df, -7.0 / 3.0);
+    const cudaStream_t s = b->stream;
+    int32_t *d_t = nullptr;
+    uint64_t *d_u = nullptr;
+    double *d_out = nullptr;
+    std::vector<double> out(3 * n);
+    cudaError_t e = cudaMalloc(&d_t, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_u, sizeof(uint64_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_t, ht.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_u, hu.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_band(fused_args(b, b->d_iota, 0), b->d_prefix, b->d_khi0, d_t, d_u, (int)n, ka, kb, b->d_scales,
+                        zfac, sfac, d_out, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), d_out, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);
+    cui_status st = e == cudaSuccess ? sync_and_check(b) : cuda_fail(e, "band sums");
+    cudaFree(d_t);
+    cudaFree(d_u);
+    cudaFree(d_out);
+    if (st != CUI_OK) return st;
+    for (int64_t i = 0; i < n; ++i) {
+        host_z[2 * i] = out[3 * i];
+        host_z[2 * i + 1] = out[3 * i + 1];
+        if (host_sigma2) host_sigma2[i] = out[3 * i + 2];
+    }
+    return CUI_OK;
 }
 
 extern "C" cui_status cui_td_template(cui_bank b, int64_t t, int32_t pn_x2, double *hp_dev, double *hx_dev)

@@ -775,37 +775,127 @@ cudaError_t launch_template_out(const FusedArgs &a, int t, const double *amp, do
     return cudaGetLastError();
 }
 
+// ------------------------------------------------- direct band sums ----
+constexpr int kSumWarps = 8; // warps of a direct-sum CTA
+
+// This thread's share of sum_{ka <= k < kb} q_k exp(2 pi i k u / 2^64), with
+// q_k generated exactly as pass 1 generates it (same anchors, cubic and
+// exact-phase table) and the time u a 64-bit fraction of the segment (sample
+// s is u = s 2^64 / N).  Lane j of a warp evaluates the anchor of block
+// base + j; the warp then sweeps those blocks of C bins.
+__device__ float2 band_sum(const FusedArgs &p, int t, const float2 *cdf, int ka, int kb, uint64_t u)
+{
+    float2 acc = make_float2(0.f, 0.f);
+    if (kb <= ka) return acc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int C = p.ccols, kex = p.kex[t];
+    const int B0 = ka / C, B1 = (kb - 1) / C;
+    for (int base = B0 + warp * 32; base <= B1; base += kSumWarps * 32) {
+        float4 anc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (base + lane <= B1) anc = anchor_eval(p, t, base + lane, (float)((int64_t)(base + lane) * C + C / 2));
+        const int nb = min(32, B1 - base + 1);
+        for (int j = 0; j < nb; ++j) {
+            const float4 a = make_float4(__shfl_sync(0xffffffffu, anc.x, j), __shfl_sync(0xffffffffu, anc.y, j),
+                                         __shfl_sync(0xffffffffu, anc.z, j), __shfl_sync(0xffffffffu, anc.w, j));
+            const int B = base + j;
+            for (int x = lane; x < C; x += 32) {
+                const int k = B * C + x;
+                if (k < ka || k >= kb) continue;
+                const float2 w = p.wbar[k];
+                const float2 q = k < kex ? rotate(phase_exact(cdf, p.gexact + (int64_t)k * kNB), w)
+                                         : gen_bin(a, (float)(x - C / 2), w);
+                // the turn k u / 2^64 mod 1, from the top 32 bits of k u mod 2^64, in [-1/2, 1/2)
+                const float fr = (float)(int32_t)(uint32_t)(((uint64_t)k * u) >> 32) * 2.3283064365386963e-10f;
+                float sn, cs;
+                __sincosf(6.283185307179586f * fr, &sn, &cs);
+                const float2 v = cmul(q, make_float2(cs, sn));
+                acc.x += v.x;
+                acc.y += v.y;
+            }
+        }
+    }
+    return acc;
+}
+
+// The CTA's sum of every thread's value, in a fixed order; valid in thread 0.
+__device__ float2 cta_sum(float2 acc, float2 *part)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    float2 z = make_float2(0.f, 0.f);
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kSumWarps; ++w) z = z + part[w];
+    __syncthreads();
+    return z;
+}
+
+// Band correlator at arbitrary times (multi-band search): query i is template
+// tmpl[i] at time u[i]; the band is [ka, min(kb, k_hi(t))) with k_hi(t) the
+// template's own upper edge (khi0, whatever band the filter calls use).
+// out[3 i .. 3 i + 2] = (Re z, Im z, sigma_B^2) in physical units:
+// z = zfac sum q_k e^(2 pi i k u) / scale_w and sigma_B^2 = sfac (Pw[kb'] - Pw[ka]).
+__global__ void __launch_bounds__(kSumWarps * 32) k_band(const FusedArgs p, const double *prefix,
+                                                        const int32_t *khi0, const int32_t *tmpl, const uint64_t *u,
+                                                        int ka, int kb, const SegScales *sc, double zfac, double sfac,
+                                                        double *out)
+{
+    __shared__ float2 cdf[kNB];
+    __shared__ float2 part[kSumWarps];
+    const int i = blockIdx.x;
+    const int t = tmpl[i];
+    const int kh = min(kb, khi0[t]);
+    if (threadIdx.x < kNB) cdf[threadIdx.x] = p.coef_df[(int64_t)t * kNB + threadIdx.x];
+    __syncthreads();
+    const float2 z = cta_sum(band_sum(p, t, cdf, ka, kh, u[i]), part);
+    if (threadIdx.x == 0) {
+        const double f = zfac / sc->scale_w;
+        out[3 * (int64_t)i] = f * (double)z.x;
+        out[3 * (int64_t)i + 1] = f * (double)z.y;
+        out[3 * (int64_t)i + 2] = kh > ka ? sfac * (prefix[kh] - prefix[ka]) : 0.0;
+    }
+}
+
+cudaError_t launch_band(const FusedArgs &a, const double *prefix, const int32_t *khi0, const int32_t *tmpl,
+                        const uint64_t *u, int n, int ka, int kb, const SegScales *sc, double zfac, double sfac,
+                        double *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_band<<<n, kSumWarps * 32, 0, s>>>(a, prefix, khi0, tmpl, u, ka, kb, sc, zfac, sfac, out);
+    launched();
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------- chi^2 veto ----
 // Signal-consistency test at a trigger (template t, sample s): the template's
-// band [k_low, k_hi) is split into P sub-bands of equal template power, edges
-// k_l = min{k : Pw[k] >= (l/P) Pw[k_hi]} from the prefix sums Pw of
-// |h~_k|^2 / S_k; the sub-band correlators z_l(s) = sum_{k in band l} q_k
-// exp(2 pi i k s / N) are summed directly at s, with q_k generated exactly as
-// pass 1 generates it (same anchors, cubic and exact-phase table); then
-// chi^2 = P sum_l |z_l - z/P|^2 / sigma^2 with z = sum_l z_l.
-constexpr int kChisqWarps = 8;
-
-__global__ void __launch_bounds__(kChisqWarps * 32) k_chisq(const FusedArgs p, const double *prefix, const int2 *trig,
-                                                           int P, float *chisq, float *rho)
+// band [k_low, k_hi) (as the filter calls use it) is split into P sub-bands of
+// equal template power, edges k_l = min{k : Pw[k] - Pw[k_low] >= (l/P)
+// (Pw[k_hi] - Pw[k_low])} from the prefix sums Pw of |h~_k|^2 / S_k; the
+// sub-band correlators z_l(s) = sum_{k in band l} q_k exp(2 pi i k s / N) are
+// summed directly at s; then chi^2 = P sum_l |z_l - z/P|^2 / sigma^2 with
+// z = sum_l z_l.
+__global__ void __launch_bounds__(kSumWarps * 32) k_chisq(const FusedArgs p, const double *prefix, const int2 *trig,
+                                                         int P, float *chisq, float *rho)
 {
     __shared__ int bnd[kChisqMaxBands + 1];
     __shared__ float2 cdf[kNB];
-    __shared__ float2 part[kChisqWarps];
+    __shared__ float2 part[kSumWarps];
     __shared__ float2 zl[kChisqMaxBands];
     const int i = blockIdx.x;
     const int t = trig[i].x;
-    const int64_t smp = trig[i].y;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int klo = p.k_low, khi = max(p.khi[t], klo), kex = p.kex[t];
-    const int C = p.ccols;
-    const int64_t N = p.n;
+    const uint64_t u = (uint64_t)(uint32_t)trig[i].y << (64 - p.log2n);
+    const int klo = p.k_low, khi = max(p.khi[t], klo);
     if (threadIdx.x < kNB) cdf[threadIdx.x] = p.coef_df[(int64_t)t * kNB + threadIdx.x];
     if (threadIdx.x <= P) {
         const int l = threadIdx.x;
         int e = l == 0 ? klo : khi;
         if (l > 0 && l < P) {
-            // smallest k in [klo, khi] with prefix[k] >= (l/P) prefix[khi] (prefix[klo] = 0)
-            const double target = prefix[khi] * (double)l / (double)P;
+            // smallest k in [klo, khi] with Pw[k] - Pw[klo] >= (l/P) (Pw[khi] - Pw[klo])
+            const double target = prefix[klo] + (prefix[khi] - prefix[klo]) * (double)l / (double)P;
             int lo = klo, hi = khi;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
@@ -818,51 +908,8 @@ __global__ void __launch_bounds__(kChisqWarps * 32) k_chisq(const FusedArgs p, c
     }
     __syncthreads();
     for (int l = 0; l < P; ++l) {
-        const int ka = bnd[l], kb = bnd[l + 1];
-        float2 acc = make_float2(0.f, 0.f);
-        if (kb > ka) {
-            const int B0 = ka / C, B1 = (kb - 1) / C; // blocks of C bins, anchored at their centres
-            for (int base = B0 + warp * 32; base <= B1; base += kChisqWarps * 32) {
-                // lane j evaluates the anchor of block base + j; the warp then sweeps those blocks
-                float4 anc = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (base + lane <= B1)
-                    anc = anchor_eval(p, t, base + lane, (float)((int64_t)(base + lane) * C + C / 2));
-                const int nb = min(32, B1 - base + 1);
-                for (int j = 0; j < nb; ++j) {
-                    const float4 a = make_float4(__shfl_sync(0xffffffffu, anc.x, j), __shfl_sync(0xffffffffu, anc.y, j),
-                                                 __shfl_sync(0xffffffffu, anc.z, j), __shfl_sync(0xffffffffu, anc.w, j));
-                    const int B = base + j;
-                    for (int x = lane; x < C; x += 32) {
-                        const int k = B * C + x;
-                        if (k < ka || k >= kb) continue;
-                        const float2 w = p.wbar[k];
-                        const float2 q = k < kex ? rotate(phase_exact(cdf, p.gexact + (int64_t)k * kNB), w)
-                                                 : gen_bin(a, (float)(x - C / 2), w);
-                        // exp(2 pi i k s / N), from k s mod N (exact in integers)
-                        float fr = (float)(((int64_t)k * smp) & (N - 1)) / (float)N;
-                        fr -= rintf(fr);
-                        float sn, cs;
-                        __sincosf(6.283185307179586f * fr, &sn, &cs);
-                        const float2 v = cmul(q, make_float2(cs, sn));
-                        acc.x += v.x;
-                        acc.y += v.y;
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-        }
-        if (lane == 0) part[warp] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float2 z = make_float2(0.f, 0.f);
-            for (int w8 = 0; w8 < kChisqWarps; ++w8) z = z + part[w8];
-            zl[l] = z;
-        }
-        __syncthreads();
+        const float2 z = cta_sum(band_sum(p, t, cdf, bnd[l], bnd[l + 1], u), part);
+        if (threadIdx.x == 0) zl[l] = z;
     }
     if (threadIdx.x == 0) {
         float2 z = make_float2(0.f, 0.f);
@@ -882,7 +929,7 @@ cudaError_t launch_chisq(const FusedArgs &a, const double *prefix, const int2 *t
                          float *rho, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_chisq<<<n, kChisqWarps * 32, 0, s>>>(a, prefix, trig, bands, chisq, rho);
+    k_chisq<<<n, kSumWarps * 32, 0, s>>>(a, prefix, trig, bands, chisq, rho);
     launched();
     return cudaGetLastError();
 }

@@ -56,11 +56,16 @@ void launch_fft_passes_f32(float2 *a, float2 *b, int log2n, int sign, const Twid
 void launch_segment_transform_df(const double *d, double2 *a, double2 *b, int log2n, const Twiddles &tw,
                                  cudaStream_t s, double2 **result);
 void launch_amp_table(double *amp, int64_t nhalf, cudaStream_t s);
+// the segment restricted to bins [ka, kb) below m/2, m = 2^log2m <= n samples
+// at the rate fs n / m; X the segment's bins 0 .. n/2, a and b m elements each
+void launch_band_series(const double2 *X, int64_t n, int log2m, int64_t ka, int64_t kb, const Twiddles &tw,
+                        dfc *a, dfc *b, double *out, cudaStream_t s);
 void launch_weighted_data(const double2 *X, const double *psd, const double *amp, int64_t n, int k_low,
                           double fs, SegScales *scales, float2 *wbar, void *dS, bool dS_fp64, cudaStream_t s);
 void launch_prefix(const double *psd, const double *amp, int64_t n, int k_low, double *prefix, double *work,
                    cudaStream_t s);
-void launch_template_norm(const double *prefix, const int32_t *khi, int64_t nt, double fs, int64_t n,
+// sigma^2 and the fused normaliser of every template over [klo, khi[t])
+void launch_template_norm(const double *prefix, const int32_t *khi, int klo, int64_t nt, double fs, int64_t n,
                           const SegScales *scales, double *sigma2, float *invnorm, cudaStream_t s);
 void launch_basis_table(double *g, float2 *g_df, int n1, int n2, int ccols, cudaStream_t s);
 void launch_exact_table(float2 *g, int kx, cudaStream_t s);
@@ -105,6 +110,11 @@ cudaError_t launch_chisq(const FusedArgs &a, const double *prefix, const int2 *t
                          float *rho, cudaStream_t s);
 cudaError_t launch_template_out(const FusedArgs &a, int t, const double *amp, double dfac, float2 *out,
                                 cudaStream_t s);
+// band correlator of n queries (tmpl[i], time u[i] as a 64-bit fraction of the
+// segment) over [ka, min(kb, khi0[t])): out[3 i ..] = (Re z, Im z, sigma_B^2)
+cudaError_t launch_band(const FusedArgs &a, const double *prefix, const int32_t *khi0, const int32_t *tmpl,
+                        const uint64_t *u, int n, int ka, int kb, const SegScales *sc, double zfac, double sfac,
+                        double *out, cudaStream_t s);
 
 struct FinalizeArgs {
     const int32_t *order;    // device template order

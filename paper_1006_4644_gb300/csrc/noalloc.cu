@@ -121,7 +121,8 @@ extern "C" cui_status cui_template_sigma_noalloc(const double *psd_dev, int64_t 
     if (e != cudaSuccess) return noalloc_fail(CUI_ERR_CUDA, cudaGetErrorString(e));
     launch_amp_table(sc->amp, nh, s);
     launch_prefix(psd_dev, sc->amp, n, k_low, sc->prefix, sc->bsum, s);
-    launch_template_norm(sc->prefix, sc->khi, count, sample_rate, n, &sc->scales, sigma2_dev, sc->invnorm, s);
+    launch_template_norm(sc->prefix, sc->khi, k_low, count, sample_rate, n, &sc->scales, sigma2_dev, sc->invnorm,
+                         s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(CUI_ERR_CUDA, cudaGetErrorString(e));
     return CUI_OK;

@@ -164,6 +164,47 @@ void launch_segment_transform_df(const double *d, double2 *a, double2 *b, int lo
     *result = reinterpret_cast<double2 *>(r);
 }
 
+// ------------------------------------------------- band-limited series ---
+// Y_k' (k' < m = N / decim) = X_k' on the band, its Hermitian mirror above
+// m / 2, zero elsewhere (and at m / 2), as double-float scaled by 2^kDfShift.
+__global__ void k_band_spectrum(const double2 *__restrict__ X, dfc *__restrict__ Y, int64_t m, int64_t ka,
+                                int64_t kb)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = j <= m / 2 ? j : m - j;
+        dfc y = {df{0.f, 0.f}, df{0.f, 0.f}};
+        if (k >= ka && k < kb && k < m / 2) {
+            const double2 x = X[k];
+            y = dfc{split_double(x.x), split_double(j <= m / 2 ? x.y : -x.y)};
+        }
+        Y[j] = y;
+    }
+}
+
+// out_j = Re(Y_j) 2^-kDfShift / n, j < m
+__global__ void k_dfc_real_out(const dfc *__restrict__ Y, double *__restrict__ out, int64_t m, double inv_n)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        out[j] = ldexp((double)Y[j].x.hi + (double)Y[j].x.lo, -kDfShift) * inv_n;
+}
+
+// x'_j = (1/N) sum over the band's bins k (and mirrors) of X_k e^(2 pi i k j / m),
+// j < m = N / decim: the segment restricted to bins [ka, kb) below m / 2 at
+// the sample rate fs / decim.  a and b hold m double-float values each.  The
+// Stockham twiddles depend only on the sub-transform sizes, so the bank's
+// tables (built for N) serve the shorter transform.
+void launch_band_series(const double2 *X, int64_t n, int log2m, int64_t ka, int64_t kb, const Twiddles &tw,
+                        dfc *a, dfc *b, double *out, cudaStream_t s)
+{
+    const int64_t m = int64_t(1) << log2m;
+    k_band_spectrum<<<1216, 256, 0, s>>>(X, a, m, ka, kb);
+    launched();
+    dfc *r = nullptr;
+    fft_passes<df>(a, b, log2m, +1, TwTab<df>{tw.lodf, tw.hidf, tw.shift, tw.log2n}, s, &r, 1, kDfLog2Radix);
+    k_dfc_real_out<<<1216, 256, 0, s>>>(r, out, m, 1.0 / (double)n);
+    launched();
+}
+
 // lo[i] = exp(2 pi i i / 2^log2n), hi[i] = exp(2 pi i (i << shift) / 2^log2n), in FP64 and FP32
 __global__ void k_twiddle_tables(Twiddles t)
 {
@@ -376,28 +417,29 @@ void launch_prefix(const double *psd, const double *amp, int64_t n, int k_low, d
     launched(3);
 }
 
-// sigma^2_t = 4 df df^(-7/3) P[k_hi(t)] (the amplitude law's df^(-7/6) factor
-// squared) and the fused path's normaliser 4 df / (scale_w^2 P[k_hi]).
-__global__ void k_tnorm(const double *prefix, const int32_t *khi, int64_t nt, int64_t nh, double df, double dfp,
-                        const SegScales *sc, double *sigma2, float *invnorm)
+// sigma^2_t = 4 df df^(-7/3) (P[k_hi(t)] - P[klo]) (the amplitude law's
+// df^(-7/6) factor squared) and the fused path's normaliser
+// 4 df / (scale_w^2 (P[k_hi] - P[klo])); klo >= the segment's k_low.
+__global__ void k_tnorm(const double *prefix, const int32_t *khi, int klo, int64_t nt, int64_t nh, double df,
+                        double dfp, const SegScales *sc, double *sigma2, float *invnorm)
 {
     const double sw = sc->scale_w;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
         int64_t kh = khi[t];
         kh = kh < 0 ? 0 : (kh > nh ? nh : kh);
-        double P = prefix[kh];
+        double P = kh > klo ? prefix[kh] - prefix[klo] : 0.0;
         sigma2[t] = 4.0 * df * dfp * P;
         invnorm[t] = P > 0.0 ? (float)(4.0 * df / (sw * sw * P)) : 0.0f;
     }
 }
 
-void launch_template_norm(const double *prefix, const int32_t *khi, int64_t nt, double fs, int64_t n,
+void launch_template_norm(const double *prefix, const int32_t *khi, int klo, int64_t nt, double fs, int64_t n,
                           const SegScales *scales, double *sigma2, float *invnorm, cudaStream_t s)
 {
     const double df = fs / (double)n;
     const double dfp = pow(df, -7.0 / 3.0);
     const int blocks = (int)((nt + 255) / 256);
-    k_tnorm<<<blocks < 1216 ? blocks : 1216, 256, 0, s>>>(prefix, khi, nt, n / 2, df, dfp, scales, sigma2, invnorm);
+    k_tnorm<<<blocks < 1216 ? blocks : 1216, 256, 0, s>>>(prefix, khi, klo, nt, n / 2, df, dfp, scales, sigma2, invnorm);
     launched();
 }
 
