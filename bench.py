@@ -278,6 +278,106 @@ def run_stream(args, w):
     return 0
 
 
+def run_extras(args, w):
+    """Rates of the steps that follow the filter: cross-template clustering,
+    the chi^2 test, the time-domain generator, the band sums and series of the
+    multi-band search (all on --workload), then the multi-band hierarchical
+    search over one 1024 s segment from 10 Hz (the long-template workload),
+    against the exhaustive full-band filter of the same templates."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1006_4644_gb300 import Bank
+    from paper_1006_4644_gb300.multiband import hierarchical_search
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+
+    def cuda_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps, 1e3 * (time.perf_counter() - t0) / reps
+
+    def dev(x):
+        x = np.array(x, dtype=np.float64)
+        x[0] = 1.0  # bin 0 is never read
+        return torch.from_numpy(x).cuda()
+
+    out = {"metric": "rates of the post-filter steps and the multi-band search", "n_gpus": 1, "data": "synthetic"}
+    m1, m2 = w.masses()
+    psd = w.psd()
+    with Bank(m1, m2, n=w.n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, snr_threshold=5.0,
+              stream=stream.cuda_stream) as bank:
+        strain = torch.from_numpy(build_segment(w, bank, psd)).cuda()
+        bank.upload(strain, dev(psd))
+        bank.filter()
+        trig, total = bank.triggers()
+        _, ms = cuda_ms(lambda: bank.clustered_triggers(), 20)
+        out["cluster"] = {"ms_per_readout": ms, "triggers": int(total)}
+        pick = trig[np.arange(256) % len(trig)]
+        ms, _ = cuda_ms(lambda: bank.trigger_chisq(pick, 16), 5)
+        out["chisq"] = {"triggers_per_s": 256 / (ms / 1e3), "bands": 16, "triggers_per_call": 256}
+        pk = bank.peaks()
+        times = pk["sample"] / w.fs
+        tm = np.arange(w.n_templates)
+        ms, _ = cuda_ms(lambda: bank.band_correlate(tm, times), 5)
+        out["band_correlate"] = {"queries_per_s": w.n_templates / (ms / 1e3), "band": "full"}
+        series = torch.empty(w.n, dtype=torch.float64, device="cuda")
+        ms1, _ = cuda_ms(lambda: bank.band_series(series, 40.0, 0.0, 1), 10)
+        ms8, _ = cuda_ms(lambda: bank.band_series(series[: w.n // 8], 0.0, 40.0, 8), 10)
+        out["band_series_ms"] = {"decim_1": ms1, "decim_8": ms8}
+        hp = torch.empty(w.n, dtype=torch.float64, device="cuda")
+        hx = torch.empty(w.n, dtype=torch.float64, device="cuda")
+        ms, _ = cuda_ms(lambda: [bank.td_template(t, hp, hx) for t in range(64)], 3)
+        out["td_template"] = {"templates_per_s": 64 / (ms / 1e3), "n": w.n, "pn_order": 2.5}
+
+    # multi-band hierarchical search: 256 templates of the long-template
+    # workload (f_low 10 Hz, chirps up to ~30 min) over one 1024 s segment
+    wl = synth.WORKLOADS["seg1024s_bank1m_et"]
+    l1, l2 = wl.masses()
+    l1, l2 = l1[:256], l2[:256]
+    f_split, ns, valid = 40.0, 1 << 19, (48 * 4096, 1 << 19)
+    kw = dict(fs=wl.fs, f_low=wl.f_low, pn_x2=wl.pn_x2, stream=stream.cuda_stream)
+    psd_l = wl.psd()
+    with Bank(l1, l2, n=wl.n, **kw) as seg, \
+            Bank(l1, l2, n=ns, snr_threshold=8.0, valid=valid, **kw) as det:
+        d = wl.noise(0)
+        seg.upload(torch.from_numpy(synth.strain_from_spectrum(d, wl.n, wl.fs)).cuda(), dev(psd_l))
+        sig = seg.sigma()
+        h = torch.zeros(wl.n // 2 + 1, dtype=torch.complex64, device="cuda")
+        seg.template(0, h)
+        j0 = 700 * 4096
+        synth.add_signal(d, h.cpu().numpy().astype(np.complex128), 15.0 / sig[0], j0, wl.n)
+        strain_l = torch.from_numpy(synth.strain_from_spectrum(d, wl.n, wl.fs)).cuda()
+        psd_d, psd_s = dev(psd_l), dev(synth.psd_onesided(ns, wl.fs, wl.psd_scale))
+        seg.upload(strain_l, psd_d)
+        cand = hierarchical_search(seg, det, f_split, psd_s)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cand = hierarchical_search(seg, det, f_split, psd_s)
+        torch.cuda.synchronize()
+        t_hier = time.perf_counter() - t0
+        ms_full, _ = cuda_ms(lambda: seg.filter(), 2)
+        hit = cand[(cand["tmpl"] == 0) & (np.abs(cand["t"] * wl.fs - j0) <= 2)]
+        out["hierarchical"] = {
+            "workload": f"256 templates of {wl.name}, one {wl.n} sample segment, split at {f_split} Hz, "
+                        f"upper band on {ns}-sample segments valid on [{valid[0]}, {valid[1]})",
+            "seconds": t_hier, "templates_per_s": 256 / t_hier, "candidates": int(len(cand)),
+            "injection_rho": float(hit["rho"].max()) if len(hit) else None, "injected_snr": 15.0,
+            "exhaustive_full_band_seconds": ms_full / 1e3,
+            "note": "the full-band filter of the 2^22-sample segment wraps every chirp longer than 1024 s"}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -290,6 +390,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--tuning", default=None, help="fixed tiling n1,ccols,rpc,batch (skips the autotuner)")
+    ap.add_argument("--extras", action="store_true",
+                    help="instead of the step benchmark, time clustering, chi^2, the time-domain generator and "
+                         "the multi-band search")
     ap.add_argument("--stream", type=int, default=0,
                     help="instead of the step benchmark, stream this many overlapping segments of --workload")
     args = ap.parse_args()
@@ -302,6 +405,8 @@ def main():
         return run_reference(args, w)
     if args.stream > 0:
         return run_stream(args, w)
+    if args.extras:
+        return run_extras(args, w)
 
     import numpy as np
     import torch

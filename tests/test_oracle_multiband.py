@@ -2,7 +2,8 @@
 correlator against the FFT route at sample times and, between samples, against
 the FFT route of a zero-padded spectrum; the band edges on single bins; bands
 adding up; the exact band SNR of a bank-member injection; the band-limited
-filter; and the same sums from a decimated copy of the segment."""
+filter; the same sums from a decimated copy of the segment; and the
+band-limited, resampled series on sums of cosines."""
 
 import math
 
