@@ -1,9 +1,10 @@
 """Multi-band search on the GPU: the band-limited filter (cui_bank_set_band)
 against the oracle's band filter; the band correlators at arbitrary times
 (cui_band_correlate) against the oracle's direct sums and against the filter's
-own peaks; the band-limited, resampled series (cui_segment_band_series)
-against the oracle's; and the hierarchical search recovering a chirp that is
-longer than the short segments its upper band is searched on."""
+own peaks, at 2^16 and sampled at 2^20; the band-limited, resampled series
+(cui_segment_band_series) against the oracle's; and the hierarchical search
+recovering a chirp that is longer than the short segments its upper band is
+searched on."""
 
 import math
 
@@ -34,13 +35,15 @@ def _bank(w, **kw):
     return Bank(m1, m2, n=w.n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, **kw)
 
 
-@pytest.mark.parametrize("band", [(60.0, 0.0), (45.0, 150.0)])
-def test_band_filter_matches_the_oracle(band):
+@pytest.mark.parametrize("band,plain", [((60.0, 0.0), False), ((45.0, 150.0), False), ((60.0, 0.0), True)])
+def test_band_filter_matches_the_oracle(band, plain):
+    from paper_1006_4644_gb300 import CUI_PLAIN
+
     w = W16
     strain, psd, dt, _ = make_segment(w)
     m1, m2 = w.masses()
     thr = 4.5
-    with _bank(w, snr_threshold=thr) as b:
+    with _bank(w, snr_threshold=thr, flags=CUI_PLAIN if plain else 0) as b:
         b.upload(strain, psd)
         b.filter()
         full = b.peaks()
@@ -95,6 +98,24 @@ def test_band_correlate_matches_the_oracle():
     assert np.allclose(rho, pk["snr"], rtol=2e-4)
     dphi = np.angle(np.exp(1j * (np.angle(z) - pk["phase"])))
     assert np.max(np.abs(dphi)) < 2e-3
+
+
+def test_band_correlate_at_2p20_sampled():
+    w = synth.WORKLOADS["seg256s_bank1024_pn35"]
+    strain, psd, dt, (tmpl, j0, _) = make_segment(w)
+    m1, m2 = w.masses()
+    rng = np.random.default_rng(9)
+    tm = np.concatenate([tmpl[:3], rng.integers(0, w.n_templates, 5)]).astype(np.int32)
+    ts = np.concatenate([j0[:3] / w.fs, rng.uniform(0.0, w.n / w.fs, 5)])
+    with _bank(w) as b:
+        b.upload(strain, psd)
+        z, s2 = b.band_correlate(tm, ts, 0.0, 100.0)
+    for i in range(len(tm)):
+        t = int(tm[i])
+        zo, so = oracle.band_correlate(dt, psd, m1[t], m2[t], w.pn_x2, w.f_low, w.fs, w.n, [ts[i]], 0.0, 100.0)
+        assert abs(s2[i] - so) <= 1e-9 * so
+        sg = math.sqrt(so)
+        assert abs(z[i] - zo[0]) <= 1e-3 * sg * max(1.0, abs(zo[0]) / sg), (i, z[i], zo[0])
 
 
 @pytest.mark.parametrize("band,decim", [((60.0, 0.0), 1), ((0.0, 60.0), 8), ((20.0, 300.0), 4)])
