@@ -135,31 +135,52 @@ __device__ __forceinline__ df split_double(double x)
     return {ldexpf(hi1, e - 1023 + kDfShift), ldexpf(lo1, e - 1075 + kDfShift)};
 }
 
-__global__ void k_real_to_dfc(const double *__restrict__ d, dfc *__restrict__ out, int64_t n)
+// z_m = d_2m + i d_2m+1 (x 2^kDfShift), m < M = N/2: the real segment as M
+// complex values, so that one M-point transform serves it
+__global__ void k_real_pairs_to_dfc(const double *__restrict__ d, dfc *__restrict__ out, int64_t m)
 {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-        out[j] = dfc{split_double(d[j]), df{0.f, 0.f}};
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        out[j] = dfc{split_double(d[2 * j]), split_double(d[2 * j + 1])};
 }
 
-// bins 0 .. n-1 back to FP64 in place (only the one-sided half is read later)
-__global__ void k_dfc_to_double(dfc *io, int64_t n)
+// X_k, k = 0 .. M, from Z = DFT_M(z), in place (Z_k becomes X_k; slot M is
+// written too).  With E and O the transforms of the even and odd samples,
+// Z_k = E_k + i O_k and conj(Z_{M-k}) = E_k - i O_k, so E_k = (Z_k +
+// conj(Z_{M-k}))/2, O_k = -i (Z_k - conj(Z_{M-k}))/2, X_k = E_k + W^k O_k and
+// X_{M-k} = conj(E_k - W^k O_k), W = e^(-2 pi i / N).  Thread k does k and M-k.
+__global__ void k_real_post(dfc *io, int64_t m, const TwTab<df> tw)
 {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        const dfc v = io[j];
-        reinterpret_cast<double2 *>(io)[j] = make_double2(ldexp((double)v.x.hi + (double)v.x.lo, -kDfShift),
-                                                          ldexp((double)v.y.hi + (double)v.y.lo, -kDfShift));
+    const df half = {0.5f, 0.0f};
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= m / 2;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const dfc a = io[k];
+        const dfc zc = io[k == 0 ? 0 : m - k];
+        const dfc b = {zc.x, -zc.y}; // conj(Z_{M-k})
+        const dfc e = {(a.x + b.x) * half, (a.y + b.y) * half};
+        const dfc o = {(a.y - b.y) * half, (b.x - a.x) * half}; // -i (a - b) / 2
+        const dfc t = cmul(o, tab_turn<df, -1>(tw, k));
+        const dfc lo = e + t, hi = e - t;
+        double2 *out = reinterpret_cast<double2 *>(io);
+        out[k] = make_double2(ldexp((double)lo.x.hi + (double)lo.x.lo, -kDfShift),
+                              ldexp((double)lo.y.hi + (double)lo.y.lo, -kDfShift));
+        if (k != m - k)
+            out[m - k] = make_double2(ldexp((double)hi.x.hi + (double)hi.x.lo, -kDfShift),
+                                      -ldexp((double)hi.y.hi + (double)hi.y.lo, -kDfShift));
     }
 }
 
+// X_k = sum_j d_j e^(-2 pi i jk/N) for k = 0 .. N/2, as FP64, in a or b: an
+// N/2-point double-float transform of the sample pairs, then the split above.
 void launch_segment_transform_df(const double *d, double2 *a, double2 *b, int log2n, const Twiddles &tw,
                                  cudaStream_t s, double2 **result)
 {
-    const int64_t n = int64_t(1) << log2n;
+    const int64_t m = int64_t(1) << (log2n - 1);
     dfc *da = reinterpret_cast<dfc *>(a), *db = reinterpret_cast<dfc *>(b), *r = nullptr;
-    k_real_to_dfc<<<1216, 256, 0, s>>>(d, da, n);
+    const TwTab<df> tt{tw.lodf, tw.hidf, tw.shift, tw.log2n};
+    k_real_pairs_to_dfc<<<1216, 256, 0, s>>>(d, da, m);
     launched();
-    fft_passes<df>(da, db, log2n, -1, TwTab<df>{tw.lodf, tw.hidf, tw.shift, tw.log2n}, s, &r, 1, kDfLog2Radix);
-    k_dfc_to_double<<<1216, 256, 0, s>>>(r, n / 2 + 1);
+    fft_passes<df>(da, db, log2n - 1, -1, tt, s, &r, 1, kDfLog2Radix);
+    k_real_post<<<1216, 256, 0, s>>>(r, m, tt);
     launched();
     *result = reinterpret_cast<double2 *>(r);
 }
@@ -247,29 +268,38 @@ void launch_amp_table(double *amp, int64_t nh, cudaStream_t s)
     launched();
 }
 
-__device__ __forceinline__ double warp_max_d(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
+// Band maxima of |d~ amp / S| and |d~ / S|, to a power of two: only the
+// scale below is taken from them, so integer operations on the exponent
+// fields replace the FP64 arithmetic (the slow path on this GPU).  With e(v)
+// the exponent of v, the estimate 2^(e(max(|Re X|, |Im X|)) - e(S) [+ e(amp)]
+// + e(1/fs)) lies within a factor 2^-1 .. 2^3.5 of the true maximum.
+// Non-negative doubles compare as unsigned integers, so atomicMax on their
+// bits is a floating-point max.
+__device__ __forceinline__ int exp_field(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF); }
 
-// Band maxima of |d~ amp / S| and |d~ / S| (non-negative doubles compare as
-// unsigned integers, so atomicMax on their bits is a floating-point max).
 __global__ void k_wmax(const double2 *__restrict__ X, const double *__restrict__ psd, const double *__restrict__ amp,
-                       int64_t nh, int k_low, double inv_fs, SegScales *sc)
+                       int64_t nh, int k_low, int e_fs, SegScales *sc)
 {
-    double mw = 0.0, md = 0.0;
+    constexpr int kNone = -(1 << 20);
+    int ew = kNone, ed = kNone;
     for (int64_t k = k_low + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nh;
          k += (int64_t)gridDim.x * blockDim.x) {
-        double2 x = X[k];
-        double a = hypot(x.x, x.y) * inv_fs / psd[k];
-        md = fmax(md, a);
-        mw = fmax(mw, a * amp[k]);
+        const double2 x = X[k];
+        const long long bx = __double_as_longlong(x.x) & 0x7FFFFFFFFFFFFFFFll;
+        const long long by = __double_as_longlong(x.y) & 0x7FFFFFFFFFFFFFFFll;
+        const int ex = (int)((bx > by ? bx : by) >> 52); // 0 for zero (and subnormal) bins
+        if (ex == 0) continue;
+        const int d = ex - exp_field(psd[k]);
+        ed = max(ed, d);
+        ew = max(ew, d + exp_field(amp[k]) - 1023);
     }
-    mw = warp_max_d(mw);
-    md = warp_max_d(md);
-    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, o));
+        ed = max(ed, __shfl_xor_sync(0xffffffffu, ed, o));
+    }
+    if ((threadIdx.x & 31) == 0 && ed != kNone) {
+        const double mw = ldexp(1.0, ew + e_fs), md = ldexp(1.0, ed + e_fs);
         atomicMax((unsigned long long *)&sc->max_w, (unsigned long long)__double_as_longlong(mw));
         atomicMax((unsigned long long *)&sc->max_d, (unsigned long long)__double_as_longlong(md));
     }
@@ -311,7 +341,7 @@ void launch_weighted_data(const double2 *X, const double *psd, const double *amp
 {
     const int64_t nh = n / 2;
     cudaMemsetAsync(scales, 0, sizeof(SegScales), s);
-    k_wmax<<<1216, 256, 0, s>>>(X, psd, amp, nh, k_low, 1.0 / fs, scales);
+    k_wmax<<<1216, 256, 0, s>>>(X, psd, amp, nh, k_low, ilogb(1.0 / fs), scales);
     k_wwrite<<<1216, 256, 0, s>>>(X, psd, amp, nh, k_low, 1.0 / fs, scales, wbar, dS, dS_fp64);
     launched(2);
 }
