@@ -216,8 +216,12 @@ struct cui_bank_s {
     int32_t *d_order = nullptr;
     int64_t order_cap = 0;
     bool have_segment = false, have_peaks = false;
-    // CUDA graph of the last fused filter call and its signature
-    cudaStream_t cap_stream = nullptr;
+    // CUDA graph of the last fused filter call and its signature; the capture
+    // forks onto a second stream so that pass 1 of a batch overlaps pass 2 of
+    // the previous one (two Y buffers, events fork / p1[2] / p2[2] / join)
+    cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+    cudaEvent_t gev[6] = {};
+    int ny = 1; // Y buffers: 2 when a call can hold more than one batch
     GraphKey gkey = {};
     cudaGraphExec_t gexec = nullptr;
     long long glaunches = 0;
@@ -308,6 +312,9 @@ static void release(cui_bank b)
     for (cudaEvent_t e : b->pool) cudaEventDestroy(e);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->cap_stream2) cudaStreamDestroy(b->cap_stream2);
+    for (cudaEvent_t ev : b->gev)
+        if (ev) cudaEventDestroy(ev);
     if (b->h_stage) cudaFreeHost(b->h_stage);
 }
 
@@ -371,7 +378,8 @@ static cudaError_t configure_fused(cui_bank b, const cui_tuning &tu)
     b->rpc = tu.rpc;
     b->batch = (int)std::min<int64_t>(tu.batch, b->nt);
     const size_t per = (size_t)b->n * ((b->desc.flags & CUI_STORE_BF16) ? 4 : 8);
-    if ((e = cudaMalloc(&b->d_y, per * (size_t)b->batch)) != cudaSuccess) return e;
+    b->ny = b->nt > b->batch ? 2 : 1;
+    if ((e = cudaMalloc(&b->d_y, per * (size_t)b->batch * b->ny)) != cudaSuccess) return e;
     if ((e = dalloc(&b->d_win, (int64_t)b->batch * std::max(1, b->nwin))) != cudaSuccess) return e;
     e = cudaMemsetAsync(b->d_win, 0, sizeof(Slot) * (size_t)b->batch * std::max(1, b->nwin), s);
     if (e != cudaSuccess) return e;
@@ -480,6 +488,8 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     chk(dalloc(&b->d_err, 1));
     chk(cudaMallocHost(&b->h_stage, sizeof(*b->h_stage)));
     chk(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    chk(cudaStreamCreateWithFlags(&b->cap_stream2, cudaStreamNonBlocking));
+    for (cudaEvent_t &ev : b->gev) chk(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     b->h_c0.resize(nt);
     for (int64_t t = 0; t < nt; ++t) b->h_c0[t] = coef[t * kNB];
     if (b->fused) {
@@ -691,6 +701,37 @@ static cudaError_t enqueue_fused(cui_bank b, const int32_t *d_ord, int64_t count
     return cudaSuccess;
 }
 
+// The same with pass 1 of batch i on stream sa and pass 2 + finalize on sb:
+// pass 1 of batch i + 1 runs while pass 2 of batch i reads the other Y
+// buffer.  Only under graph capture (the events order the two streams).
+static cudaError_t enqueue_fused_overlap(cui_bank b, const int32_t *d_ord, int64_t count, cui_peak *pout,
+                                         cudaStream_t sa, cudaStream_t sb)
+{
+    FinalizeArgs fa = finalize_args(b, d_ord, pout);
+    cudaEvent_t fork = b->gev[0], join = b->gev[1], *p1 = b->gev + 2, *p2 = b->gev + 4;
+    const size_t slice = (size_t)b->n * ((b->desc.flags & CUI_STORE_BF16) ? 4 : 8) * (size_t)b->batch;
+    cudaError_t e;
+    if ((e = cudaEventRecord(fork, sa)) != cudaSuccess || (e = cudaStreamWaitEvent(sb, fork, 0)) != cudaSuccess)
+        return e;
+    int i = 0;
+    for (int64_t base = 0; base < count; base += b->batch, ++i) {
+        const int bc = (int)std::min<int64_t>(b->batch, count - base);
+        FusedArgs a = fused_args(b, d_ord, base);
+        a.ywork = (char *)b->d_y + (size_t)(i & 1) * slice;
+        if (i >= 2 && (e = cudaStreamWaitEvent(sa, p2[i & 1], 0)) != cudaSuccess) return e; // batch i-2 has read it
+        if ((e = launch_pass1(a, bc, sa)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(p1[i & 1], sa)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sb, p1[i & 1], 0)) != cudaSuccess) return e;
+        if ((e = launch_pass2(a, bc, sb)) != cudaSuccess) return e;
+        fa.base = base;
+        fa.count = bc;
+        if ((e = launch_finalize(fa, sb)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(p2[i & 1], sb)) != cudaSuccess) return e;
+    }
+    if ((e = cudaEventRecord(join, sb)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(sa, join, 0);
+}
+
 extern "C" cui_status cui_filter_bank(cui_bank b, const int32_t *order, int64_t count, cui_peak *peaks_dev)
 {
     if (!b) return fail(CUI_ERR_ARG, "bank is NULL");
@@ -728,7 +769,11 @@ extern "C" cui_status cui_filter_bank(cui_bank b, const int32_t *order, int64_t 
             const long long l0 = g_launches.load();
             CUI_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture");
             cudaError_t e1 = reset_call_outputs(b, b->cap_stream);
-            cudaError_t e2 = e1 == cudaSuccess ? enqueue_fused(b, d_ord, count, pout, b->cap_stream) : e1;
+            cudaError_t e2 = e1;
+            if (e1 == cudaSuccess)
+                e2 = b->ny > 1 && count > b->batch
+                         ? enqueue_fused_overlap(b, d_ord, count, pout, b->cap_stream, b->cap_stream2)
+                         : enqueue_fused(b, d_ord, count, pout, b->cap_stream);
             cudaGraph_t graph = nullptr;
             cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &graph);
             if (e2 != cudaSuccess || e3 != cudaSuccess) {
