@@ -367,11 +367,14 @@ def run_extras(args, w):
         t_hier = time.perf_counter() - t0
         ms_full, _ = cuda_ms(lambda: seg.filter(), 2)
         hit = cand[(cand["tmpl"] == 0) & (np.abs(cand["t"] * wl.fs - j0) <= 2)]
+        best = hit[np.argmax(hit["rho"])] if len(hit) else None
+        zf, sf = seg.band_correlate([0], [best["t"]]) if best is not None else (np.zeros(1), np.ones(1))
         out["hierarchical"] = {
             "workload": f"256 templates of {wl.name}, one {wl.n} sample segment, split at {f_split} Hz, "
                         f"upper band on {ns}-sample segments valid on [{valid[0]}, {valid[1]})",
             "seconds": t_hier, "templates_per_s": 256 / t_hier, "candidates": int(len(cand)),
-            "injection_rho": float(hit["rho"].max()) if len(hit) else None, "injected_snr": 15.0,
+            "injection_rho": float(best["rho"]) if best is not None else None, "injected_snr": 15.0,
+            "injection_rho_full_band_whole_segment": float(abs(zf[0]) / np.sqrt(sf[0])) if best is not None else None,
             "exhaustive_full_band_seconds": ms_full / 1e3,
             "note": "the full-band filter of the 2^22-sample segment wraps every chirp longer than 1024 s"}
     print(json.dumps(out), flush=True)
