@@ -110,11 +110,13 @@ cui_status cui_bank_create(const cui_bank_desc *desc, const double *m1, const do
  * read and must be finite and > 0).  on_device = 1 means both pointers are
  * device memory, 0 host memory (pinned host memory makes the copies
  * asynchronous).  Computes d~ (double-float transform, FP64 result), the
- * noise-weighted data and every template's sigma^2 on the device.
+ * noise-weighted data and every template's sigma^2 on the device.  A host PSD
+ * is checked on the device: the call queues all of its work, then waits until
+ * the GPU has checked the PSD (the work queued behind the check goes on).
+ * Device PSDs are not checked and the call does not wait.
  * Errors: CUI_ERR_ARG (n != desc.n, n_psd != N/2 + 1, NULL pointers; a host
  * PSD bin in the band that is not finite and > 0, which leaves the bank
- * without a segment until the next successful upload; device PSDs are not
- * checked), CUI_ERR_CUDA.  Paper: the data chunk X(f) and S_n(f) of
+ * without a segment until the next successful upload), CUI_ERR_CUDA.  Paper: the data chunk X(f) and S_n(f) of
  * eq:matchedfilter. */
 cui_status cui_segment_upload(cui_bank bank, const double *strain, int64_t n, const double *psd,
                               int64_t n_psd, int on_device);

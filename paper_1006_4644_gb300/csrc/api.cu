@@ -7,7 +7,6 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -212,7 +211,10 @@ struct cui_bank_s {
     struct Stage {
         int err, pad;
         unsigned long long trig_count;
-    } *h_stage = nullptr; // pinned: read back with one synchronisation
+        unsigned long long psd_bad; // first bad PSD bin of the last host upload, ~0 if none
+    } *h_stage = nullptr;           // pinned: read back with one synchronisation
+    unsigned long long *d_psd_bad = nullptr;
+    cudaEvent_t ev_psd = nullptr;
     int32_t *d_order = nullptr;
     int64_t order_cap = 0;
     bool have_segment = false, have_peaks = false;
@@ -302,7 +304,7 @@ static void release(cui_bank b)
                     b->tw.lo64, b->tw.hi64, b->tw.lo32, b->tw.hi32, b->tw.lodf, b->tw.hidf,
                     b->d_wbar, b->d_dS, b->d_scales, b->d_basis, b->d_basis_df, b->d_kex, b->d_gexact, b->d_y,
                     b->d_win, b->d_h, b->d_qa, b->d_qb, b->d_acc, b->d_pwin, b->d_cluster, b->d_trig, b->d_trig_count, b->d_err,
-                    b->d_order};
+                    b->d_order, b->d_psd_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &m : b->marks) {
@@ -316,6 +318,7 @@ static void release(cui_bank b)
     for (cudaEvent_t ev : b->gev)
         if (ev) cudaEventDestroy(ev);
     if (b->h_stage) cudaFreeHost(b->h_stage);
+    if (b->ev_psd) cudaEventDestroy(b->ev_psd);
 }
 
 extern "C" const char *cui_last_error(void) { return g_err.c_str(); }
@@ -487,6 +490,8 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     chk(dalloc(&b->d_cluster, std::max(1, b->nwin)));
     chk(dalloc(&b->d_err, 1));
     chk(cudaMallocHost(&b->h_stage, sizeof(*b->h_stage)));
+    chk(dalloc(&b->d_psd_bad, 1));
+    chk(cudaEventCreateWithFlags(&b->ev_psd, cudaEventDisableTiming));
     chk(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
     chk(cudaStreamCreateWithFlags(&b->cap_stream2, cudaStreamNonBlocking));
     for (cudaEvent_t &ev : b->gev) chk(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -550,32 +555,6 @@ extern "C" void cui_bank_destroy(cui_bank b)
     delete b;
 }
 
-// True when every psd[k], lo <= k < hi, is finite and > 0.  A branch-free
-// scan split over a few host threads: it is memory-bound and runs while the
-// GPU transforms the strain.
-static bool psd_band_ok(const double *psd, int64_t lo, int64_t hi)
-{
-    constexpr int kThreads = 4;
-    unsigned bad[kThreads] = {};
-    auto scan = [&](int i) {
-        const int64_t a = lo + (hi - lo) * i / kThreads, e = lo + (hi - lo) * (i + 1) / kThreads;
-        unsigned acc = 0;
-        for (int64_t k = a; k < e; ++k) acc |= (unsigned)!(psd[k] > 0.0 && psd[k] <= DBL_MAX);
-        bad[i] = acc;
-    };
-    if (hi - lo < (int64_t(1) << 16)) {
-        for (int i = 0; i < kThreads; ++i) scan(i);
-    } else {
-        std::thread th[kThreads - 1];
-        for (int i = 1; i < kThreads; ++i) th[i - 1] = std::thread(scan, i);
-        scan(0);
-        for (auto &t : th) t.join();
-    }
-    unsigned any = 0;
-    for (unsigned v : bad) any |= v;
-    return any == 0;
-}
-
 extern "C" cui_status cui_segment_upload(cui_bank b, const double *strain, int64_t n, const double *psd,
                                          int64_t n_psd, int on_device)
 {
@@ -585,21 +564,22 @@ extern "C" cui_status cui_segment_upload(cui_bank b, const double *strain, int64
     if (n_psd != b->nh + 1) return fail(CUI_ERR_ARG, "n_psd must be N/2 + 1 = %lld", (long long)(b->nh + 1));
     const cudaStream_t s = b->stream;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    // The data transform needs only the strain: it is queued first, so that the
-    // host checks the PSD while the GPU transforms.
+    // Everything is queued before the host waits: a host PSD is checked on the
+    // device (one pass over the band) and the host waits for that check only,
+    // while the GPU goes on with the weighting queued behind it.
     CUI_TRY(cudaMemcpyAsync(b->d_strain, strain, sizeof(double) * b->n, kind, s), "strain copy");
     Span span(b, 0);
     double2 *X = nullptr;
     launch_segment_transform_df(b->d_strain, b->d_fa, b->d_fb, b->log2n, b->tw, s, &X);
-    if (!on_device) {
-        if (!psd_band_ok(psd, b->k_low, b->nh)) {
-            b->have_segment = false; // the transform queued above replaced the previous segment's
-            for (int64_t k = b->k_low; k < b->nh; ++k)
-                if (!(psd[k] > 0) || !std::isfinite(psd[k]))
-                    return fail(CUI_ERR_ARG, "psd[%lld] must be finite and > 0 in the band", (long long)k);
-        }
-    }
     CUI_TRY(cudaMemcpyAsync(b->d_psd, psd, sizeof(double) * (b->nh + 1), kind, s), "psd copy");
+    if (!on_device) {
+        CUI_TRY(cudaMemsetAsync(b->d_psd_bad, 0xFF, sizeof(unsigned long long), s), "psd check");
+        launch_psd_check(b->d_psd, b->k_low, b->nh, b->d_psd_bad, s);
+        CUI_TRY(cudaMemcpyAsync(&b->h_stage->psd_bad, b->d_psd_bad, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, s),
+                "psd check");
+        CUI_TRY(cudaEventRecord(b->ev_psd, s), "psd check");
+    }
     b->d_X = X;
     launch_weighted_data(X, b->d_psd, b->d_amp, b->n, b->k_low, b->desc.sample_rate, b->d_scales, b->d_wbar,
                          b->d_dS, b->plain_fp64, s);
@@ -607,6 +587,14 @@ extern "C" cui_status cui_segment_upload(cui_bank b, const double *strain, int64
     launch_template_norm(b->d_prefix, b->d_khi, b->band_lo, b->nt, b->desc.sample_rate, b->n, b->d_scales,
                          b->d_sigma2, b->d_invnorm, s);
     CUI_TRY(cudaGetLastError(), "cui_segment_upload");
+    if (!on_device) {
+        CUI_TRY(cudaEventSynchronize(b->ev_psd), "psd check");
+        const unsigned long long k = b->h_stage->psd_bad;
+        if (k != ~0ull) {
+            b->have_segment = false; // the data queued above replaced the previous segment's
+            return fail(CUI_ERR_ARG, "psd[%llu] must be finite and > 0 in the band", k);
+        }
+    }
     b->have_segment = true;
     b->filtered = false;
     return CUI_OK;

@@ -56,6 +56,8 @@ void launch_fft_passes_f32(float2 *a, float2 *b, int log2n, int sign, const Twid
 void launch_segment_transform_df(const double *d, double2 *a, double2 *b, int log2n, const Twiddles &tw,
                                  cudaStream_t s, double2 **result);
 void launch_amp_table(double *amp, int64_t nhalf, cudaStream_t s);
+// lowest k in [k_lo, k_hi) with psd[k] not finite and > 0 into *bad (atomicMin; preset to ~0)
+void launch_psd_check(const double *psd, int64_t k_lo, int64_t k_hi, unsigned long long *bad, cudaStream_t s);
 // the segment restricted to bins [ka, kb) below m/2, m = 2^log2m <= n samples
 // at the rate fs n / m; X the segment's bins 0 .. n/2, a and b m elements each
 void launch_band_series(const double2 *X, int64_t n, int log2m, int64_t ka, int64_t kb, const Twiddles &tw,

@@ -3,6 +3,7 @@
 // sums, and the template-independent tables (amplitude law, anchor basis).
 // Also the generic multi-pass Stockham FFT over global memory that the
 // segment transform and the per-template plain path use.
+#include <cfloat>
 #include <cstdio>
 
 #include "internal.h"
@@ -265,6 +266,22 @@ __global__ void k_amp(double *amp, int64_t nh)
 void launch_amp_table(double *amp, int64_t nh, cudaStream_t s)
 {
     k_amp<<<1216, 256, 0, s>>>(amp, nh);
+    launched();
+}
+
+// The lowest k in [k_lo, k_hi) whose psd[k] is not finite and > 0, into
+// *bad (preset to all ones by the caller), by atomicMin.
+__global__ void k_psd_check(const double *__restrict__ psd, int64_t k_lo, int64_t k_hi, unsigned long long *bad)
+{
+    for (int64_t k = k_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < k_hi;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double v = psd[k];
+        if (!(v > 0.0 && v <= DBL_MAX)) atomicMin(bad, (unsigned long long)k);
+    }
+}
+void launch_psd_check(const double *psd, int64_t k_lo, int64_t k_hi, unsigned long long *bad, cudaStream_t s)
+{
+    k_psd_check<<<1216, 256, 0, s>>>(psd, k_lo, k_hi, bad);
     launched();
 }
 
