@@ -504,6 +504,14 @@ def main():
             "both_passes": {"achieved": n_units * 2 * per_tmpl / ((p1[2] + p2[2]) / 1e3) / 1e9,
                             "frac": n_units * 2 * per_tmpl / ((p1[2] + p2[2]) / 1e3) / 1e9 / peak},
             "kernel_ms": {k: v[2] for k, v in trace.items()}}
+    # secondary roof: the transform's 5 N log2 N flops per template (mostly adds
+    # that cannot fuse) against one FP32 operation per lane per clock
+    flop = 5.0 * w.n * math.log2(w.n) * n_units
+    alu_peak = 152 * 128 * 2.07e9 / 1e12
+    roof["alu_secondary"] = {"flop_per_template": 5.0 * w.n * math.log2(w.n),
+                             "achieved_tflops": flop / ((p1[2] + p2[2]) / 1e3) / 1e12, "peak_tflops": alu_peak,
+                             "frac": flop / ((p1[2] + p2[2]) / 1e3) / 1e12 / alu_peak,
+                             "peak_basis": "152 SMs x 128 FP32 lanes x 2.07 GHz, one add per lane per clock"}
 
     # end to end through the public API with pinned host buffers
     strain_h = torch.from_numpy(strain).pin_memory()
