@@ -60,21 +60,23 @@ __global__ void k_td_template(const TdArgs a, double *hp, double *hx)
         const double t = -(double)((a.n - j) % a.n) / a.fs;
         double p = 0.0, x = 0.0;
         if (j != 0 && t >= a.t_lo && t <= a.t_hi) {
-            // Newton on t(v) = t from the Newtonian inverse
-            double v = pow(5.0 * a.M / (256.0 * a.eta * -t), 0.125);
+            // Newton on t(v) = t from the Newtonian inverse (integer powers by
+            // products: FP64 pow is the slow path on this GPU)
+            double v = sqrt(sqrt(sqrt(5.0 * a.M / (256.0 * a.eta * -t))));
             v = fmin(fmax(v, a.v_lo), a.v_hi);
             for (int it = 0; it < 12; ++it) {
-                const double v8 = pow(v, 8.0);
+                const double v2 = v * v, v4 = v2 * v2, v8 = v4 * v4;
                 const double g = poly(a.ct, a.kmax, v) / v8 - t;
                 const double dv = g / (poly(a.cd, a.kmax, v) / (v8 * v));
                 v = fmin(fmax(v - dv, a.v_lo), a.v_hi);
                 if (fabs(dv) <= 1e-15 * v) break;
             }
-            const double phi = poly(a.cp, a.kmax, v) / pow(v, 5.0) + a.clog * log(v);
+            const double v2 = v * v;
+            const double phi = poly(a.cp, a.kmax, v) / (v2 * v2 * v) + a.clog * log(v);
             double s, c;
             sincos(2.0 * phi, &s, &c);
-            p = v * v * c;
-            x = v * v * s;
+            p = v2 * c;
+            x = v2 * s;
         }
         hp[j] = p;
         hx[j] = x;
