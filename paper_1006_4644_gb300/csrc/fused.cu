@@ -776,21 +776,22 @@ cudaError_t launch_template_out(const FusedArgs &a, int t, const double *amp, do
 }
 
 // ------------------------------------------------- direct band sums ----
-constexpr int kSumWarps = 8; // warps of a direct-sum CTA
+constexpr int kSumWarps = 8;    // warps of a band-correlator CTA (one query each)
+constexpr int kChisqWarps = 32; // warps of a chi^2 CTA (one trigger each: fewer, longer CTAs)
 
 // This thread's share of sum_{ka <= k < kb} q_k exp(2 pi i k u / 2^64), with
 // q_k generated exactly as pass 1 generates it (same anchors, cubic and
 // exact-phase table) and the time u a 64-bit fraction of the segment (sample
 // s is u = s 2^64 / N).  Lane j of a warp evaluates the anchor of block
 // base + j; the warp then sweeps those blocks of C bins.
-__device__ float2 band_sum(const FusedArgs &p, int t, const float2 *cdf, int ka, int kb, uint64_t u)
+template <int NW> __device__ float2 band_sum(const FusedArgs &p, int t, const float2 *cdf, int ka, int kb, uint64_t u)
 {
     float2 acc = make_float2(0.f, 0.f);
     if (kb <= ka) return acc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int C = p.ccols, kex = p.kex[t];
     const int B0 = ka / C, B1 = (kb - 1) / C;
-    for (int base = B0 + warp * 32; base <= B1; base += kSumWarps * 32) {
+    for (int base = B0 + warp * 32; base <= B1; base += NW * 32) {
         float4 anc = make_float4(0.f, 0.f, 0.f, 0.f);
         if (base + lane <= B1) anc = anchor_eval(p, t, base + lane, (float)((int64_t)(base + lane) * C + C / 2));
         const int nb = min(32, B1 - base + 1);
@@ -851,7 +852,7 @@ __global__ void __launch_bounds__(kSumWarps * 32) k_band(const FusedArgs p, cons
     const int kh = min(kb, khi0[t]);
     if (threadIdx.x < kNB) cdf[threadIdx.x] = p.coef_df[(int64_t)t * kNB + threadIdx.x];
     __syncthreads();
-    const float2 z = cta_sum(band_sum(p, t, cdf, ka, kh, u[i]), part);
+    const float2 z = cta_sum(band_sum<kSumWarps>(p, t, cdf, ka, kh, u[i]), part);
     if (threadIdx.x == 0) {
         const double f = zfac / sc->scale_w;
         out[3 * (int64_t)i] = f * (double)z.x;
@@ -878,12 +879,12 @@ cudaError_t launch_band(const FusedArgs &a, const double *prefix, const int32_t 
 // sub-band correlators z_l(s) = sum_{k in band l} q_k exp(2 pi i k s / N) are
 // summed directly at s; then chi^2 = P sum_l |z_l - z/P|^2 / sigma^2 with
 // z = sum_l z_l.
-__global__ void __launch_bounds__(kSumWarps * 32) k_chisq(const FusedArgs p, const double *prefix, const int2 *trig,
-                                                         int P, float *chisq, float *rho)
+__global__ void __launch_bounds__(kChisqWarps * 32) k_chisq(const FusedArgs p, const double *prefix, const int2 *trig,
+                                                           int P, float *chisq, float *rho)
 {
     __shared__ int bnd[kChisqMaxBands + 1];
     __shared__ float2 cdf[kNB];
-    __shared__ float2 part[kSumWarps];
+    __shared__ float2 part[kChisqMaxBands][kChisqWarps];
     __shared__ float2 zl[kChisqMaxBands];
     const int i = blockIdx.x;
     const int t = trig[i].x;
@@ -907,10 +908,24 @@ __global__ void __launch_bounds__(kSumWarps * 32) k_chisq(const FusedArgs p, con
         bnd[l] = e;
     }
     __syncthreads();
+    // every warp sweeps every sub-band and keeps its own partial sums: no
+    // barrier until all sub-bands are done; then the same fixed-order sums as cta_sum
     for (int l = 0; l < P; ++l) {
-        const float2 z = cta_sum(band_sum(p, t, cdf, bnd[l], bnd[l + 1], u), part);
-        if (threadIdx.x == 0) zl[l] = z;
+        float2 acc = band_sum<kChisqWarps>(p, t, cdf, bnd[l], bnd[l + 1], u);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if ((threadIdx.x & 31) == 0) part[l][threadIdx.x >> 5] = acc;
     }
+    __syncthreads();
+    if (threadIdx.x < P) {
+        float2 z = make_float2(0.f, 0.f);
+        for (int w = 0; w < kChisqWarps; ++w) z = z + part[threadIdx.x][w];
+        zl[threadIdx.x] = z;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         float2 z = make_float2(0.f, 0.f);
         for (int l = 0; l < P; ++l) z = z + zl[l];
@@ -929,7 +944,7 @@ cudaError_t launch_chisq(const FusedArgs &a, const double *prefix, const int2 *t
                          float *rho, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_chisq<<<n, kSumWarps * 32, 0, s>>>(a, prefix, trig, bands, chisq, rho);
+    k_chisq<<<n, kChisqWarps * 32, 0, s>>>(a, prefix, trig, bands, chisq, rho);
     launched();
     return cudaGetLastError();
 }
