@@ -268,8 +268,8 @@ __global__ void __launch_bounds__(C *N1 / 16, p1_min_blocks(C *N1 / 16)) k_pass1
             anc[g][a] = anchor_eval(p, t, ai, (float)((int64_t)n2 * a + b0 + C / 2));
         }
     }
-    if (tid < G * kNB && tid / kNB < ng)
-        cdf[tid / kNB][tid % kNB] = p.coef_df[(int64_t)p.order[p.base + y0 + tid / kNB] * kNB + tid % kNB];
+    for (int m = tid; m < ng * kNB; m += NT) // a CTA can have fewer threads than G kNB
+        cdf[m / kNB][m % kNB] = p.coef_df[(int64_t)p.order[p.base + y0 + m / kNB] * kNB + m % kNB];
     __syncthreads();
 
     for (int g = 0; g < ng; ++g) {
@@ -633,7 +633,7 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-constexpr int kPass1Group = 8;    // templates per pass-1 CTA (2 -> 2.24, 4 -> 2.07, 8 -> 2.02 us at 2^20)
+constexpr int kPass1Group = 8;    // templates per pass-1 CTA (2 -> 2.24, 4 -> 2.07, 8 -> 2.02, 16 -> 2.12 us at 2^20)
 constexpr int kPairMaxL = 8192;   // pass 2 runs on row pairs up to this row length
 
 static bool paired(int n2) { return n2 <= kPairMaxL; }

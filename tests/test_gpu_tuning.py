@@ -54,6 +54,33 @@ def test_every_tiling_matches_the_oracle(log2n):
             assert rep.ok(), (n1, cc, rpc, rep)
 
 
+@pytest.mark.parametrize("n1,cc", list(itertools.product([64, 128, 256], [16, 32, 64])))
+def test_full_template_groups_match_the_oracle(n1, cc):
+    """Batches that fill every pass-1 CTA with its full group of templates, at
+    the smallest CTAs (n1 = 64 with 16 columns is 64 threads)."""
+    from paper_1006_4644_gb300 import Bank, CuiError
+
+    n = 1 << 14
+    w = synth.Workload("tile14g", n, 4096.0, 30.0, 7, 40, 1.0, 8.0, False, 1, 15.0, 15.0, 1.0, 521)
+    strain, psd, dt, _ = make_segment(w)
+    m1, m2 = w.masses()
+    with Bank(m1, m2, n=n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, snr_threshold=5.0) as b:
+        b.upload(strain, psd)
+        for rpc in (1, 2, 4, 8, 16, 32):
+            try:
+                b.set_tuning(n1, cc, rpc, w.n_templates)
+                break
+            except CuiError:
+                continue
+        else:
+            pytest.skip("no pass-2 tiling for this n1")
+        b.filter()
+        peaks = b.peaks()
+        trig, _ = b.triggers()
+    rep = compare_bank(w, dt, psd, peaks, trig, range(w.n_templates), 0, n, int(w.fs), 5.0)
+    assert rep.ok(), (n1, cc, rep)
+
+
 def test_autotune_selects_a_valid_tiling():
     from paper_1006_4644_gb300 import Bank, CuiError
 
