@@ -1,10 +1,10 @@
 """Multi-band search on the GPU: the band-limited filter (cui_bank_set_band)
 against the oracle's band filter; the band correlators at arbitrary times
 (cui_band_correlate) against the oracle's direct sums and against the filter's
-own peaks, at 2^16 and sampled at 2^20; the band-limited, resampled series
-(cui_segment_band_series) against the oracle's; and the hierarchical search
-recovering a chirp that is longer than the short segments its upper band is
-searched on."""
+own peaks, at 2^16 and sampled at 2^20; the band filter sampled at 2^20; the
+band-limited, resampled series (cui_segment_band_series) against the oracle's at
+2^16 and 2^20; and the hierarchical search recovering a chirp that is longer
+than the short segments its upper band is searched on."""
 
 import math
 
@@ -67,6 +67,32 @@ def test_band_filter_matches_the_oracle(band, plain):
     assert len(trig) > 0
 
 
+def test_band_filter_at_2p20_sampled():
+    """The band-limited filter at the full size of the 1024-template, 2^20-sample
+    workload (its own tiling), against the oracle's band filter on sampled
+    templates, including the injected ones."""
+    w = synth.WORKLOADS["seg256s_bank1024_pn35"]
+    strain, psd, dt, (tmpl, _, _) = make_segment(w)
+    m1, m2 = w.masses()
+    band, thr = (80.0, 0.0), 5.5
+    with _bank(w, snr_threshold=thr) as b:
+        b.upload(strain, psd)
+        b.set_band(*band)
+        b.filter()
+        peaks, (trig, _), sig = b.peaks(), b.triggers(), b.sigma()
+    per = split_triggers(trig, w.n_templates)
+    pick = sorted(set(int(t) for t in tmpl) | set(np.random.default_rng(3).integers(0, w.n_templates, 8).tolist()))
+    rep = Report()
+    for t in pick:
+        h, _, _ = oracle.spa_template(m1[t], m2[t], w.pn_x2, w.f_low, w.fs, w.n)
+        ka, kb = oracle.band_edges(m1[t], m2[t], w.f_low, w.fs, w.n, *band)
+        s2 = oracle.sigma2(h, psd, w.fs, w.n, ka, kb)
+        assert abs(sig[t] - math.sqrt(s2)) <= 1e-9 * math.sqrt(s2)
+        z = oracle.correlate(dt, h, psd, w.fs, w.n, ka, kb)
+        check_template(rep, t, z, np.abs(z) ** 2 / s2, peaks[t], per[t], 0, w.n, int(w.fs), thr)
+    assert not rep.errors, rep.errors[:5]
+
+
 def test_band_correlate_matches_the_oracle():
     w = W16
     strain, psd, dt, _ = make_segment(w)
@@ -118,11 +144,14 @@ def test_band_correlate_at_2p20_sampled():
         assert abs(z[i] - zo[0]) <= 1e-3 * sg * max(1.0, abs(zo[0]) / sg), (i, z[i], zo[0])
 
 
-@pytest.mark.parametrize("band,decim", [((60.0, 0.0), 1), ((0.0, 60.0), 8), ((20.0, 300.0), 4)])
-def test_band_series_matches_the_oracle(band, decim):
+@pytest.mark.parametrize("band,decim,wname", [((60.0, 0.0), 1, "seg16s_bank64_pn2"), ((0.0, 60.0), 8, "seg16s_bank64_pn2"),
+                                              ((20.0, 300.0), 4, "seg16s_bank64_pn2"),
+                                              ((40.0, 0.0), 1, "seg256s_bank1024_pn35"),
+                                              ((0.0, 40.0), 8, "seg256s_bank1024_pn35")])
+def test_band_series_matches_the_oracle(band, decim, wname):
     import torch
 
-    w = W16
+    w = synth.WORKLOADS[wname]
     strain, psd, _, _ = make_segment(w)
     with _bank(w) as b:
         b.upload(strain, psd)
