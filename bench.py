@@ -236,7 +236,7 @@ def run_stream(args, w):
     # graph is worth capturing for a handful of segments
     bank = Bank(m1, m2, valid=(n // 4, 3 * n // 4), flags=CUI_NO_GRAPH, **kw)
     bank.set_tuning(**tuning)
-    ps = Prescreen(n=n, fs=w.fs, f_low=w.f_low, bands=8, frame=n // 256, regions=100, max_batch=1,
+    ps = Prescreen(n=n, fs=w.fs, f_low=w.f_low, bands=16, frame=n // 256, regions=100, max_batch=1,
                    stream=stream.cuda_stream)
     setup_s = time.perf_counter() - t0
     feat = torch.empty((1, ps.bands, ps.frames), dtype=torch.float32, device="cuda")

@@ -239,11 +239,12 @@ class Prescreen:
     arrays are torch tensors (float32 features [count, bands, frames], targets
     and scores [count, regions]; complex128 data spectra [count, n/2 + 1])."""
 
-    def __init__(self, *, n: int, fs: float, f_low: float, bands: int = 8, frame: int = 512, regions: int = 100,
+    def __init__(self, *, n: int, fs: float, f_low: float, bands: int = 16, frame: int | None = None, regions: int = 100,
                  max_batch: int = 256, lr: float = 1e-3, betas=(0.9, 0.999), eps: float = 1e-8, seed: int = 1,
                  stream=None):
         self._l = _lib.load_prescreen(_lib.load())
         d = _lib.cui_prescreen_desc()
+        frame = max(1, int(n) // 256) if frame is None else frame  # the finest frames the network takes
         d.n, d.sample_rate, d.f_low, d.bands, d.frame, d.regions = int(n), float(fs), float(f_low), bands, frame, regions
         d.max_batch, d.lr, d.beta1, d.beta2, d.eps, d.seed = max_batch, lr, betas[0], betas[1], eps, int(seed)
         d.stream = _current_stream() if stream is None else int(stream)

@@ -1,7 +1,7 @@
 """Evaluation of the learned prescreen on the stated prescreen workload (run on
 a GPU machine; not collected by pytest):
 
-    python tests/prescreen_config4.py [--train 200000] [--test 1000] [--epochs 6]
+    python tests/prescreen_config4.py [--train 200000] [--test 1000] [--epochs 20] [--bands 16] [--frame 256]
 
 The network is trained on the GPU with oracle-made injections (one per 16 s
 segment, N = 2^16 at 4096 Hz, SNR uniform in [6, 20], masses log-uniform in
@@ -40,10 +40,12 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=200_000)
     ap.add_argument("--test", type=int, default=1000)
-    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--bands", type=int, default=16)
+    ap.add_argument("--frame", type=int, default=256)
     args = ap.parse_args()
 
     import multiprocessing as mp
@@ -68,17 +70,18 @@ def main():
     ps_ = psd.copy()
     ps_[0] = 1.0
     psd_d = torch.from_numpy(ps_).cuda()
-    rep = {"n": n, "templates": len(m1), "regions": R, "train": args.train, "test": args.test, "epochs": args.epochs}
+    rep = {"n": n, "bands": args.bands, "frame": args.frame, "templates": len(m1), "regions": R, "train": args.train,
+           "test": args.test, "epochs": args.epochs}
 
-    with Prescreen(n=n, fs=fs, f_low=f_low, bands=8, frame=512, regions=R, max_batch=args.batch, lr=args.lr,
-                   seed=1) as p:
+    with Prescreen(n=n, fs=fs, f_low=f_low, bands=args.bands, frame=args.frame, regions=R, max_batch=args.batch,
+                   lr=args.lr, seed=1) as p:
 
         def feats(start, count, keep_meta=False):
             X, Y, M, D = [], [], [], []
             for s0 in range(start, start + count, 2048):
                 d, y, meta = make_segments_mp(4, s0, min(2048, start + count - s0), n, fs, f_low, psd, bounds, R,
                                               pool=pool)
-                out = torch.zeros((len(d), 8, p.frames), dtype=torch.float32, device="cuda")
+                out = torch.zeros((len(d), p.bands, p.frames), dtype=torch.float32, device="cuda")
                 p.features(torch.from_numpy(d).cuda(), psd_d, out)
                 X.append(out)
                 Y.append(torch.from_numpy(y).cuda())
@@ -153,7 +156,7 @@ def main():
             # timing on a few held-out segments: exhaustive vs prescreen + top-K*
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             stream = torch.cuda.current_stream()
-            feat1 = torch.zeros((1, 8, p.frames), dtype=torch.float32, device="cuda")
+            feat1 = torch.zeros((1, p.bands, p.frames), dtype=torch.float32, device="cuda")
             sc1 = torch.zeros((1, R), dtype=torch.float32, device="cuda")
             t_ex, t_ps, reps = 0.0, 0.0, 8
             for i in range(reps):
