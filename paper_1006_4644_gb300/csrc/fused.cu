@@ -35,17 +35,22 @@ void fused_set_consts(const DerivConsts &dc, cudaStream_t s)
 }
 
 // ------------------------------------------------------------ storage ----
+// Y is written once by pass 1 and read once by pass 2 after the whole batch:
+// streaming accesses (evict first) keep it from displacing the weighted data
+// and the tables that every CTA reads from L2.
 template <typename ST> __device__ __forceinline__ void st_c(ST *p, float2 v);
-template <> __device__ __forceinline__ void st_c<float2>(float2 *p, float2 v) { *p = v; }
+template <> __device__ __forceinline__ void st_c<float2>(float2 *p, float2 v) { __stcs(p, v); }
 template <> __device__ __forceinline__ void st_c<__nv_bfloat162>(__nv_bfloat162 *p, float2 v)
 {
-    *p = __float22bfloat162_rn(v);
+    const __nv_bfloat162 b = __float22bfloat162_rn(v);
+    __stcs((unsigned *)p, *(const unsigned *)&b);
 }
 template <typename ST> __device__ __forceinline__ float2 ld_c(const ST *p);
-template <> __device__ __forceinline__ float2 ld_c<float2>(const float2 *p) { return *p; }
+template <> __device__ __forceinline__ float2 ld_c<float2>(const float2 *p) { return __ldcs(p); }
 template <> __device__ __forceinline__ float2 ld_c<__nv_bfloat162>(const __nv_bfloat162 *p)
 {
-    return __bfloat1622float2(*p);
+    const unsigned u = __ldcs((const unsigned *)p);
+    return __bfloat1622float2(*(const __nv_bfloat162 *)&u);
 }
 
 // Paired layout of Y: rows c and c + n1/2 of one template interleaved at each
@@ -59,22 +64,22 @@ template <typename ST> using pair_t = typename pair_of<ST>::T;
 template <typename ST> __device__ __forceinline__ void st_pair(pair_t<ST> *p, float2 lo, float2 hi);
 template <> __device__ __forceinline__ void st_pair<float2>(float4 *p, float2 lo, float2 hi)
 {
-    *p = make_float4(lo.x, hi.x, lo.y, hi.y);
+    __stcs(p, make_float4(lo.x, hi.x, lo.y, hi.y));
 }
 template <> __device__ __forceinline__ void st_pair<__nv_bfloat162>(uint2 *p, float2 lo, float2 hi)
 {
     const __nv_bfloat162 re = __floats2bfloat162_rn(lo.x, hi.x), im = __floats2bfloat162_rn(lo.y, hi.y);
-    *p = make_uint2(*(const unsigned *)&re, *(const unsigned *)&im);
+    __stcs(p, make_uint2(*(const unsigned *)&re, *(const unsigned *)&im));
 }
 template <typename ST> __device__ __forceinline__ c2 ld_pair(const pair_t<ST> *p);
 template <> __device__ __forceinline__ c2 ld_pair<float2>(const float4 *p)
 {
-    const float4 q = *p;
+    const float4 q = __ldcs(p);
     return {make_float2(q.x, q.y), make_float2(q.z, q.w)};
 }
 template <> __device__ __forceinline__ c2 ld_pair<__nv_bfloat162>(const uint2 *p)
 {
-    const uint2 q = *p;
+    const uint2 q = __ldcs(p);
     return {__bfloat1622float2(*(const __nv_bfloat162 *)&q.x), __bfloat1622float2(*(const __nv_bfloat162 *)&q.y)};
 }
 
