@@ -800,13 +800,16 @@ template <int NW> __device__ float2 band_sum(const FusedArgs &p, int t, const fl
         float4 anc = make_float4(0.f, 0.f, 0.f, 0.f);
         if (base + lane <= B1) anc = anchor_eval(p, t, base + lane, (float)((int64_t)(base + lane) * C + C / 2));
         const int nb = min(32, B1 - base + 1);
-        for (int j = 0; j < nb; ++j) {
+        // blocks of fewer than 32 bins: the warp sweeps 32 / C blocks at a time
+        const int per = C < 32 ? 32 / C : 1;
+        for (int j0 = 0; j0 < nb; j0 += per) {
+            const int j = j0 + (per > 1 ? lane / C : 0); // this lane's block (< 32)
             const float4 a = make_float4(__shfl_sync(0xffffffffu, anc.x, j), __shfl_sync(0xffffffffu, anc.y, j),
                                          __shfl_sync(0xffffffffu, anc.z, j), __shfl_sync(0xffffffffu, anc.w, j));
             const int B = base + j;
-            for (int x = lane; x < C; x += 32) {
+            for (int x = per > 1 ? lane % C : lane; x < C; x += 32) {
                 const int k = B * C + x;
-                if (k < ka || k >= kb) continue;
+                if (j >= nb || k < ka || k >= kb) continue;
                 const float2 w = p.wbar[k];
                 const float2 q = k < kex ? rotate(phase_exact(cdf, p.gexact + (int64_t)k * kNB), w)
                                          : gen_bin(a, (float)(x - C / 2), w);

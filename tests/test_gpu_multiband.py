@@ -93,7 +93,10 @@ def test_band_filter_at_2p20_sampled():
     assert not rep.errors, rep.errors[:5]
 
 
-def test_band_correlate_matches_the_oracle():
+@pytest.mark.parametrize("ccols", [16, 32, 64])
+def test_band_correlate_matches_the_oracle(ccols):
+    """Bins are generated in blocks of `ccols` (the pass-1 tiling), so every
+    block width is checked."""
     w = W16
     strain, psd, dt, _ = make_segment(w)
     m1, m2 = w.masses()
@@ -104,6 +107,7 @@ def test_band_correlate_matches_the_oracle():
     worst = 0.0
     with _bank(w) as b:
         b.upload(strain, psd)
+        b.set_tuning(64, ccols, 4, w.n_templates)
         b.set_band(100.0, 0.0)  # the filter's band does not change the band sums
         for band in ((0.0, 0.0), (0.0, 80.0), (80.0, 0.0), (55.5, 300.0)):
             z, s2 = b.band_correlate(tm, ts, *band)
