@@ -143,9 +143,10 @@ def build_segment(w, bank, psd):
     return synth.strain_from_spectrum(d, w.n, w.fs)
 
 
-def cpu_baseline(w, budget_s: float = 15.0, per_step: int | None = None):
+def cpu_baseline(w, budget_s: float = 15.0, per_step: int | None = None, strain=None):
     """The FP64 oracle as it stands, on this host's cores, on a bounded sample
-    of the same workload (noise plus oracle-built injections)."""
+    of the same workload: the given strain, else noise plus oracle-built
+    injections.  Also returns the oracle's per-template results and indices."""
     import numpy as np
 
     import oracle
@@ -154,12 +155,13 @@ def cpu_baseline(w, budget_s: float = 15.0, per_step: int | None = None):
     oracle.build()
     cores = len(os.sched_getaffinity(0))
     psd = w.psd()
-    d = w.noise()
     m1, m2 = w.masses()
-    for t, j0, snr in zip(*w.injection_plan()):
-        h, lo, hi = oracle.spa_template(m1[t], m2[t], w.pn_x2, w.f_low, w.fs, w.n)
-        synth.add_signal(d, h, float(snr) / math.sqrt(oracle.sigma2(h, psd, w.fs, w.n, lo, hi)), int(j0), w.n)
-    strain = synth.strain_from_spectrum(d, w.n, w.fs)
+    if strain is None:
+        d = w.noise()
+        for t, j0, snr in zip(*w.injection_plan()):
+            h, lo, hi = oracle.spa_template(m1[t], m2[t], w.pn_x2, w.f_low, w.fs, w.n)
+            synth.add_signal(d, h, float(snr) / math.sqrt(oracle.sigma2(h, psd, w.fs, w.n, lo, hi)), int(j0), w.n)
+        strain = synth.strain_from_spectrum(d, w.n, w.fs)
     dt = oracle.segment_spectrum(strain, w.fs)
     t0 = time.perf_counter()
     oracle.filter_template(dt, psd, m1[0], m2[0], w.pn_x2, w.f_low, w.fs, w.n)
@@ -168,11 +170,34 @@ def cpu_baseline(w, budget_s: float = 15.0, per_step: int | None = None):
         per_step = int(max(cores, min(w.n_templates, budget_s * cores / max(one, 1e-3))))
     sel = np.arange(per_step) % w.n_templates
     t0 = time.perf_counter()
-    oracle.filter_bank(dt, psd, m1[sel], m2[sel], w.pn_x2, w.f_low, w.fs, w.n, threads=cores)
+    res = oracle.filter_bank(dt, psd, m1[sel], m2[sel], w.pn_x2, w.f_low, w.fs, w.n, threads=cores)
     el = time.perf_counter() - t0
     return {"value": per_step / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{per_step} templates of {w.name} (segment FFT excluded, one template per thread)",
-            "seconds": el}
+            "seconds": el, "results": res, "templates": sel}
+
+
+def accuracy(gpu_peaks, cpu):
+    """The GPU peaks against the oracle's on the templates the CPU baseline
+    filtered (same strain and PSD): peak sample, SNR and phase."""
+    import numpy as np
+
+    seen, rel, dphi, mism = set(), [], [], 0
+    for t, r in zip(cpu["templates"], cpu["results"]):
+        t = int(t)
+        if t in seen:
+            continue
+        seen.add(t)
+        g = gpu_peaks[t]
+        rel.append(abs(float(g["snr"]) - r["peak_rho"]) / max(r["peak_rho"], 1e-30))
+        if int(g["sample"]) != int(r["peak_j"]):
+            mism += 1
+        else:
+            d = (float(g["phase"]) - r["peak_phase"] + math.pi) % (2 * math.pi) - math.pi
+            dphi.append(abs(d))
+    return {"reference": "the FP64 oracle on the same strain and PSD", "templates": len(seen),
+            "max_rel_err_snr": max(rel), "rms_rel_err_snr": float(np.sqrt(np.mean(np.square(rel)))),
+            "peak_sample_mismatches": mism, "max_phase_err_rad": max(dphi) if dphi else None}
 
 
 def run_reference(args, w):
@@ -561,10 +586,15 @@ def main():
         plain = {"value": pv, "unit": UNIT, "templates": npl, "mixed_over_plain": value / pv}
         pb.close()
 
-    cpu = None
+    cpu, acc = None, None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(w)
-        cpu.pop("seconds", None)
+        bank.upload(strain_d, psd_d)
+        bank.filter()
+        gpu_peaks = bank.peaks()
+        cpu = cpu_baseline(w, strain=strain)
+        acc = accuracy(gpu_peaks, cpu)
+        for k in ("seconds", "results", "templates"):
+            cpu.pop(k, None)
 
     bank.close()
     if rank == 0:
@@ -578,7 +608,7 @@ def main():
                            "storage": "bf16x2" if args.flags & 2 else "complex64",
                            "parallelism": f"bank replicas x{world}", "tiling": tuning},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "plain": plain, "clocks": clk.summary()}
+                "plain": plain, "accuracy": acc, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
