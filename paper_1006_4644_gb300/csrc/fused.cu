@@ -789,6 +789,20 @@ constexpr int kChisqWarps = 32; // warps of a chi^2 CTA (one trigger each: fewer
 // exact-phase table) and the time u a 64-bit fraction of the segment (sample
 // s is u = s 2^64 / N).  Lane j of a warp evaluates the anchor of block
 // base + j; the warp then sweeps those blocks of C bins.
+// q_k exp(2 pi i k u / 2^64) for one bin k of block anchor a (offset x in the block)
+__device__ __forceinline__ float2 band_term(const FusedArgs &p, const float2 *cdf, int kex, float4 a, int k, int x,
+                                            uint64_t u)
+{
+    const float2 w = p.wbar[k];
+    const float2 q = k < kex ? rotate(phase_exact(cdf, p.gexact + (int64_t)k * kNB), w)
+                             : gen_bin(a, (float)(x - p.ccols / 2), w);
+    // the turn k u / 2^64 mod 1, from the top 32 bits of k u mod 2^64, in [-1/2, 1/2)
+    const float fr = (float)(int32_t)(uint32_t)(((uint64_t)k * u) >> 32) * 2.3283064365386963e-10f;
+    float sn, cs;
+    __sincosf(6.283185307179586f * fr, &sn, &cs);
+    return cmul(q, make_float2(cs, sn));
+}
+
 template <int NW> __device__ float2 band_sum(const FusedArgs &p, int t, const float2 *cdf, int ka, int kb, uint64_t u)
 {
     float2 acc = make_float2(0.f, 0.f);
@@ -810,20 +824,88 @@ template <int NW> __device__ float2 band_sum(const FusedArgs &p, int t, const fl
             for (int x = per > 1 ? lane % C : lane; x < C; x += 32) {
                 const int k = B * C + x;
                 if (j >= nb || k < ka || k >= kb) continue;
-                const float2 w = p.wbar[k];
-                const float2 q = k < kex ? rotate(phase_exact(cdf, p.gexact + (int64_t)k * kNB), w)
-                                         : gen_bin(a, (float)(x - C / 2), w);
-                // the turn k u / 2^64 mod 1, from the top 32 bits of k u mod 2^64, in [-1/2, 1/2)
-                const float fr = (float)(int32_t)(uint32_t)(((uint64_t)k * u) >> 32) * 2.3283064365386963e-10f;
-                float sn, cs;
-                __sincosf(6.283185307179586f * fr, &sn, &cs);
-                const float2 v = cmul(q, make_float2(cs, sn));
+                const float2 v = band_term(p, cdf, kex, a, k, x, u);
                 acc.x += v.x;
                 acc.y += v.y;
             }
         }
     }
     return acc;
+}
+
+// All P sub-band sums of one trigger in one sweep over the band
+// [bnd[0], bnd[P]): warp w takes the chunks of 32 blocks w, w + NW, ... in
+// order and adds its partial sum of sub-band l into part[l][w] (lane 0 only,
+// in the warp's order) whenever its sweep leaves l, so every warp does an
+// equal share of the bins and the result does not depend on scheduling.
+template <int NW>
+__device__ void chisq_sweep(const FusedArgs &p, int t, const float2 *cdf, const int *bnd, int P, uint64_t u,
+                            float2 (*part)[NW])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ka = bnd[0], kb = bnd[P];
+    if (kb <= ka) return;
+    const int C = p.ccols, kex = p.kex[t];
+    const int B0 = ka / C, B1 = (kb - 1) / C;
+    const int per = C < 32 ? 32 / C : 1; // blocks per warp step (C <= 64: at most two bins per lane)
+    auto flush = [&](int m, float2 v) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+        }
+        if (lane == 0) part[m][warp] = part[m][warp] + v;
+    };
+    int l = 0; // the sub-band acc belongs to (the same in every lane)
+    float2 acc = make_float2(0.f, 0.f);
+    for (int base = B0 + warp * 32; base <= B1; base += NW * 32) {
+        float4 anc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (base + lane <= B1) anc = anchor_eval(p, t, base + lane, (float)((int64_t)(base + lane) * C + C / 2));
+        const int nb = min(32, B1 - base + 1);
+        for (int j0 = 0; j0 < nb; j0 += per) {
+            const int j = j0 + (per > 1 ? lane / C : 0);
+            const float4 a = make_float4(__shfl_sync(0xffffffffu, anc.x, j), __shfl_sync(0xffffffffu, anc.y, j),
+                                         __shfl_sync(0xffffffffu, anc.z, j), __shfl_sync(0xffffffffu, anc.w, j));
+            // this step's bins [k0, k1), and the sub-bands l .. le they fall in
+            const int k0 = max((base + j0) * C, ka), k1 = min((base + j0 + min(per, nb - j0)) * C, kb);
+            while (l < P - 1 && k0 >= bnd[l + 1]) {
+                flush(l, acc);
+                acc = make_float2(0.f, 0.f);
+                ++l;
+            }
+            int le = l;
+            while (le < P - 1 && k1 - 1 >= bnd[le + 1]) ++le;
+            // this lane's bins: x0 and, for 64-bin blocks, x0 + 32
+            const int x0 = per > 1 ? lane % C : lane;
+            const int B = base + j;
+            int kk0 = -1, kk1 = -1;
+            float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
+            if (j < nb) {
+                const int k = B * C + x0;
+                if (k >= ka && k < kb) {
+                    kk0 = k;
+                    v0 = band_term(p, cdf, kex, a, k, x0, u);
+                }
+                if (x0 + 32 < C && B * C + x0 + 32 >= ka && B * C + x0 + 32 < kb) {
+                    kk1 = B * C + x0 + 32;
+                    v1 = band_term(p, cdf, kex, a, kk1, x0 + 32, u);
+                }
+            }
+            if (le == l) {
+                acc = acc + v0 + v1;
+            } else { // an edge inside this step: split the lane's bins by sub-band
+                for (int m = l; m <= le; ++m) {
+                    float2 s = m == l ? acc : make_float2(0.f, 0.f);
+                    if (kk0 >= bnd[m] && kk0 < bnd[m + 1]) s = s + v0;
+                    if (kk1 >= bnd[m] && kk1 < bnd[m + 1]) s = s + v1;
+                    if (m < le) flush(m, s);
+                    else acc = s;
+                }
+                l = le;
+            }
+        }
+    }
+    flush(l, acc);
 }
 
 // The CTA's sum of every thread's value, in a fixed order; valid in thread 0.
@@ -916,17 +998,10 @@ __global__ void __launch_bounds__(kChisqWarps * 32) k_chisq(const FusedArgs p, c
         bnd[l] = e;
     }
     __syncthreads();
-    // every warp sweeps every sub-band and keeps its own partial sums: no
-    // barrier until all sub-bands are done; then the same fixed-order sums as cta_sum
-    for (int l = 0; l < P; ++l) {
-        float2 acc = band_sum<kChisqWarps>(p, t, cdf, bnd[l], bnd[l + 1], u);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-        }
-        if ((threadIdx.x & 31) == 0) part[l][threadIdx.x >> 5] = acc;
-    }
+    // each warp owns part[*][warp]: no barrier between its zeroing and its sums
+    for (int l = threadIdx.x & 31; l < P; l += 32) part[l][threadIdx.x >> 5] = make_float2(0.f, 0.f);
+    __syncwarp();
+    chisq_sweep<kChisqWarps>(p, t, cdf, bnd, P, u, part);
     __syncthreads();
     if (threadIdx.x < P) {
         float2 z = make_float2(0.f, 0.f);
