@@ -46,6 +46,7 @@ def main():
     ap.add_argument("--out", default=None)
     ap.add_argument("--bands", type=int, default=16)
     ap.add_argument("--frame", type=int, default=256)
+    ap.add_argument("--seed", type=int, default=1, help="seed of the network initialisation")
     args = ap.parse_args()
 
     import multiprocessing as mp
@@ -71,10 +72,10 @@ def main():
     ps_[0] = 1.0
     psd_d = torch.from_numpy(ps_).cuda()
     rep = {"n": n, "bands": args.bands, "frame": args.frame, "templates": len(m1), "regions": R, "train": args.train,
-           "test": args.test, "epochs": args.epochs}
+           "test": args.test, "epochs": args.epochs, "seed": args.seed}
 
     with Prescreen(n=n, fs=fs, f_low=f_low, bands=args.bands, frame=args.frame, regions=R, max_batch=args.batch,
-                   lr=args.lr, seed=1) as p:
+                   lr=args.lr, seed=args.seed) as p:
 
         def feats(start, count, keep_meta=False):
             X, Y, M, D = [], [], [], []
