@@ -2,6 +2,7 @@
 a GPU machine; not collected by pytest):
 
     python tests/prescreen_config4.py [--train 200000] [--test 1000] [--epochs 20] [--bands 16] [--frame 256]
+                                      [--seed 1] [--ensemble 3]
 
 The network is trained on the GPU with oracle-made injections (one per 16 s
 segment, N = 2^16 at 4096 Hz, SNR uniform in [6, 20], masses log-uniform in
@@ -47,6 +48,8 @@ def main():
     ap.add_argument("--bands", type=int, default=16)
     ap.add_argument("--frame", type=int, default=256)
     ap.add_argument("--seed", type=int, default=1, help="seed of the network initialisation")
+    ap.add_argument("--ensemble", type=int, default=3,
+                    help="networks trained from seeds seed, seed+1, ...; regions ranked by their mean probability")
     args = ap.parse_args()
 
     import multiprocessing as mp
@@ -72,10 +75,24 @@ def main():
     ps_[0] = 1.0
     psd_d = torch.from_numpy(ps_).cuda()
     rep = {"n": n, "bands": args.bands, "frame": args.frame, "templates": len(m1), "regions": R, "train": args.train,
-           "test": args.test, "epochs": args.epochs, "seed": args.seed}
+           "test": args.test, "epochs": args.epochs, "seed": args.seed, "ensemble": args.ensemble}
 
-    with Prescreen(n=n, fs=fs, f_low=f_low, bands=args.bands, frame=args.frame, regions=R, max_batch=args.batch,
-                   lr=args.lr, seed=args.seed) as p:
+    import contextlib
+
+    with contextlib.ExitStack() as stack:
+        nets = [stack.enter_context(Prescreen(n=n, fs=fs, f_low=f_low, bands=args.bands, frame=args.frame, regions=R,
+                                              max_batch=args.batch, lr=args.lr, seed=args.seed + e))
+                for e in range(args.ensemble)]
+        p = nets[0]  # the features do not depend on the network
+
+        def score(x, out):
+            """Mean over the networks of the region probabilities."""
+            acc = None
+            for net in nets:
+                net.scores(x, out)
+                pr = torch.softmax(out, dim=1)
+                acc = pr if acc is None else acc + pr
+            out.copy_(acc / len(nets))
 
         def feats(start, count, keep_meta=False):
             X, Y, M, D = [], [], [], []
@@ -96,19 +113,21 @@ def main():
         rep["data_s"] = time.perf_counter() - t0
         mu, sd = xtr.mean(dim=(0, 2), keepdim=True), xtr.std(dim=(0, 2), keepdim=True)
         xtr = ((xtr - mu) / sd).contiguous()
-        g = torch.Generator(device="cpu").manual_seed(0)
         t0 = time.perf_counter()
         losses = []
-        for epoch in range(args.epochs):
-            perm = torch.randperm(len(xtr), generator=g).cuda()
-            tot, nb = 0.0, 0
-            for i in range(0, len(xtr) - args.batch + 1, args.batch):
-                idx = perm[i:i + args.batch]
-                last = i + 2 * args.batch > len(xtr)
-                loss = p.train_step(xtr[idx].contiguous(), ytr[idx].contiguous(), want_loss=last)
-                if last:
-                    tot, nb = loss, 1
-            losses.append(tot / max(nb, 1))
+        for net in nets:
+            g = torch.Generator(device="cpu").manual_seed(0)
+            for epoch in range(args.epochs):
+                perm = torch.randperm(len(xtr), generator=g).cuda()
+                tot, nb = 0.0, 0
+                for i in range(0, len(xtr) - args.batch + 1, args.batch):
+                    idx = perm[i:i + args.batch]
+                    last = i + 2 * args.batch > len(xtr)
+                    loss = net.train_step(xtr[idx].contiguous(), ytr[idx].contiguous(), want_loss=last)
+                    if last:
+                        tot, nb = loss, 1
+                if net is nets[0]:
+                    losses.append(tot / max(nb, 1))
         torch.cuda.synchronize()
         rep["train_s"] = time.perf_counter() - t0
         rep["loss_by_epoch"] = losses
@@ -116,7 +135,7 @@ def main():
         xte, yte, meta, dte = feats(10_000_000, args.test, keep_meta=True)
         xte = ((xte - mu) / sd).contiguous()
         scores = torch.zeros((len(xte), R), dtype=torch.float32, device="cuda")
-        p.scores(xte, scores)
+        score(xte, scores)
         sc = scores.cpu().numpy()
         true = yte.argmax(dim=1).cpu().numpy()
         rep["recall_at"] = {k: float(np.mean([t in np.argsort(-s)[:k] for t, s in zip(true, sc)]))
@@ -168,7 +187,7 @@ def main():
                 ev[1].record(stream)
                 p.bank_features(bank, feat1)
                 feat_n = ((feat1 - mu) / sd).contiguous()
-                p.scores(feat_n, sc1)
+                score(feat_n, sc1)
                 order = ranked_order(sc1.cpu().numpy()[0], groups, k_star)
                 bank.filter(order)
                 ev[2].record(stream)
@@ -186,7 +205,7 @@ def main():
                 ev[0].record(stream)
                 for _ in range(reps):
                     p.bank_features(bank, feat1)
-                    p.scores(((feat1 - mu) / sd).contiguous(), sc1)
+                    score(((feat1 - mu) / sd).contiguous(), sc1)
                     bank.filter(order)
                 ev[1].record(stream)
                 torch.cuda.synchronize()
