@@ -10,7 +10,7 @@ import pytest
 import oracle
 import synth
 
-N, FS, F_LOW = 1 << 14, 4096.0, 30.0
+N, FS, F_LOW = 1 << 13, 4096.0, 30.0  # df = 0.5 Hz: the 4 df factor is not 1
 M1, M2, PN = 3.0, 2.0, 7
 
 
