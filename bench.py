@@ -550,8 +550,7 @@ def main():
         nonlocal n_trig
         bank2.upload(strain_h.numpy(), psd_h.numpy())
         bank2.filter()
-        bank2.peaks()
-        tr, n_trig = bank2.triggers()
+        _, tr, n_trig = bank2.results()
 
     e2e_step()
     torch.cuda.synchronize()

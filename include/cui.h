@@ -148,6 +148,16 @@ cui_status cui_peaks(cui_bank bank, cui_peak *host_out, int64_t count);
  * Paper: the candidate set {t_0^i} of step 4 and its reduction. */
 cui_status cui_triggers(cui_bank bank, cui_trigger *host_out, int64_t capacity, int64_t *n_total);
 
+/* cui_peaks and cui_triggers in one call: host_peaks[0 .. n_peaks) and up to
+ * `capacity` trigger records with their total in *n_total, as those two calls
+ * give them, read back with one synchronisation when the trigger count is at
+ * most twice the previous call's (a larger count costs a second copy).
+ * Synchronises.  Errors: as cui_peaks and cui_triggers.
+ * Paper: the per-template maxima and candidate set of step 4, read back to the
+ * host as the pipeline's result. */
+cui_status cui_results(cui_bank bank, cui_peak *host_peaks, int64_t n_peaks, cui_trigger *host_trig,
+                       int64_t capacity, int64_t *n_total);
+
 /* Cross-template clustering of the last filter call's triggers: for each
  * trigger window [valid_lo + m W, valid_lo + (m+1) W) (the same windows as
  * the per-template triggers), the loudest trigger over all filtered

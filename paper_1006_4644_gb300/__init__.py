@@ -122,6 +122,22 @@ class Bank:
         dev_cap = self.desc.trigger_capacity or (1 << 20)
         return out[: min(tot.value, capacity, dev_cap)].copy(), tot.value
 
+    def results(self, capacity: int = 1 << 20, allow_overflow: bool = False):
+        """(peaks, triggers, exact trigger total) of the last filter call, read
+        back together (cui_results: one synchronisation in the common case)."""
+        peaks = np.zeros(self.n_templates, dtype=PEAK_DTYPE)
+        buf = getattr(self, "_trig_buf", None)
+        if buf is None or len(buf) < capacity:
+            buf = self._trig_buf = np.empty(capacity, dtype=TRIGGER_DTYPE)
+        out = buf[:capacity]
+        tot = C.c_int64()
+        st = self._l.cui_results(self._h, peaks.ctypes.data, self.n_templates, out.ctypes.data, capacity,
+                                 C.byref(tot))
+        if not (allow_overflow and st == _lib.CUI_ERR_OVERFLOW):
+            _lib.check(st, "cui_results")
+        dev_cap = self.desc.trigger_capacity or (1 << 20)
+        return peaks, out[: min(tot.value, capacity, dev_cap)].copy(), tot.value
+
     def clustered_triggers(self, capacity: int = 1 << 20):
         """Loudest trigger of each window over the whole bank (last filter call),
         in increasing sample order; ties go to the lower sample, then template."""

@@ -66,6 +66,7 @@ def load():
     lib.cui_filter_bank.argtypes = [vp, vp, C.c_int64, vp]
     lib.cui_peaks.argtypes = [vp, vp, C.c_int64]
     lib.cui_triggers.argtypes = [vp, vp, C.c_int64, C.POINTER(C.c_int64)]
+    lib.cui_results.argtypes = [vp, vp, C.c_int64, vp, C.c_int64, C.POINTER(C.c_int64)]
     lib.cui_cluster_triggers.argtypes = [vp, vp, C.c_int64, C.POINTER(C.c_int64)]
     lib.cui_trigger_chisq.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, vp]
     lib.cui_td_template.argtypes = [vp, C.c_int64, C.c_int32, vp, vp]
@@ -86,7 +87,7 @@ def load():
     lib.cui_last_error.restype = C.c_char_p
     for name in ("cui_bank_create", "cui_segment_upload", "cui_filter_bank", "cui_peaks", "cui_triggers",
                  "cui_cluster_triggers", "cui_trigger_chisq", "cui_td_template", "cui_bank_set_band",
-                 "cui_band_correlate", "cui_segment_band_series",
+                 "cui_band_correlate", "cui_segment_band_series", "cui_results",
                  "cui_bank_sigma", "cui_bank_template", "cui_trace_enable", "cui_trace_read",
                  "cui_bank_get_tuning", "cui_bank_set_tuning", "cui_bank_autotune"):
         getattr(lib, name).restype = C.c_int

@@ -215,6 +215,11 @@ struct cui_bank_s {
     } *h_stage = nullptr;           // pinned: read back with one synchronisation
     unsigned long long *d_psd_bad = nullptr;
     cudaEvent_t ev_psd = nullptr;
+    // pinned read-out staging: the peaks, and a prefix of the trigger records
+    // sized from the previous count, copied in the same synchronisation
+    cui_peak *h_peaks = nullptr;
+    cui_trigger *h_trig = nullptr;
+    int64_t h_trig_cap = 0, trig_hint = 1024;
     int32_t *d_order = nullptr;
     int64_t order_cap = 0;
     bool have_segment = false, have_peaks = false;
@@ -318,6 +323,8 @@ static void release(cui_bank b)
     for (cudaEvent_t ev : b->gev)
         if (ev) cudaEventDestroy(ev);
     if (b->h_stage) cudaFreeHost(b->h_stage);
+    if (b->h_peaks) cudaFreeHost(b->h_peaks);
+    if (b->h_trig) cudaFreeHost(b->h_trig);
     if (b->ev_psd) cudaEventDestroy(b->ev_psd);
 }
 
@@ -490,6 +497,7 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     chk(dalloc(&b->d_cluster, std::max(1, b->nwin)));
     chk(dalloc(&b->d_err, 1));
     chk(cudaMallocHost(&b->h_stage, sizeof(*b->h_stage)));
+    chk(cudaMallocHost(&b->h_peaks, sizeof(cui_peak) * nt));
     chk(dalloc(&b->d_psd_bad, 1));
     chk(cudaEventCreateWithFlags(&b->ev_psd, cudaEventDisableTiming));
     chk(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
@@ -956,40 +964,81 @@ static cui_status sync_and_check(cui_bank b, unsigned long long *trig_count = nu
     return CUI_OK;
 }
 
-extern "C" cui_status cui_peaks(cui_bank b, cui_peak *host_out, int64_t count)
+// Peaks and/or triggers of the last filter call with one synchronisation in
+// the common case: the error word, the trigger count, the peaks and the first
+// records (as many as the previous call had, doubled) are copied into pinned
+// staging together; only a larger count needs a second copy.
+static cui_status read_results(cui_bank b, cui_peak *peaks_out, int64_t n_peaks, cui_trigger *trig_out,
+                               int64_t capacity, int64_t *n_total)
 {
-    if (!b || !host_out) return fail(CUI_ERR_ARG, "bank and host_out must be non-NULL");
-    if (count < 0 || count > b->nt) return fail(CUI_ERR_ARG, "count must be in [0, n_templates]");
-    if (!b->have_peaks) return fail(CUI_ERR_STATE, "no filter call kept its peaks in the handle");
-    // the copy is queued behind the filter; the error word is read in the same synchronisation
-    CUI_TRY(cudaMemcpyAsync(host_out, b->d_peaks, sizeof(cui_peak) * count, cudaMemcpyDeviceToHost, b->stream),
-            "peaks copy");
-    return sync_and_check(b);
-}
-
-extern "C" cui_status cui_triggers(cui_bank b, cui_trigger *host_out, int64_t capacity, int64_t *n_total)
-{
-    if (!b || !n_total) return fail(CUI_ERR_ARG, "bank and n_total must be non-NULL");
-    if (capacity < 0 || (capacity > 0 && !host_out)) return fail(CUI_ERR_ARG, "bad capacity / host_out");
+    const cudaStream_t s = b->stream;
+    const bool want_trig = n_total != nullptr;
+    int64_t pre = 0;
+    if (want_trig) {
+        pre = std::min<int64_t>(b->trig_cap, std::max<int64_t>(1024, 2 * b->trig_hint));
+        if (pre > b->h_trig_cap) {
+            if (b->h_trig) cudaFreeHost(b->h_trig);
+            b->h_trig = nullptr;
+            b->h_trig_cap = 0;
+            CUI_TRY(cudaMallocHost(&b->h_trig, sizeof(cui_trigger) * pre), "trigger staging");
+            b->h_trig_cap = pre;
+        }
+        CUI_TRY(cudaMemcpyAsync(b->h_trig, b->d_trig, sizeof(cui_trigger) * pre, cudaMemcpyDeviceToHost, s),
+                "trigger copy");
+    }
+    if (n_peaks > 0)
+        CUI_TRY(cudaMemcpyAsync(b->h_peaks, b->d_peaks, sizeof(cui_peak) * n_peaks, cudaMemcpyDeviceToHost, s),
+                "peaks copy");
     unsigned long long cnt = 0;
-    cui_status st = sync_and_check(b, &cnt);
-    *n_total = (int64_t)cnt;
+    cui_status st = sync_and_check(b, want_trig ? &cnt : nullptr);
+    if (want_trig) *n_total = (int64_t)cnt;
     if (st != CUI_OK) return st;
+    if (n_peaks > 0) std::memcpy(peaks_out, b->h_peaks, sizeof(cui_peak) * n_peaks);
+    if (!want_trig) return CUI_OK;
     const int64_t have = std::min<int64_t>((int64_t)cnt, b->trig_cap);
+    b->trig_hint = have;
     std::vector<cui_trigger> tmp(have);
-    if (have) CUI_TRY(cudaMemcpy(tmp.data(), b->d_trig, sizeof(cui_trigger) * have, cudaMemcpyDeviceToHost),
-                      "trigger copy");
+    if (have <= pre) {
+        if (have) std::memcpy(tmp.data(), b->h_trig, sizeof(cui_trigger) * have);
+    } else {
+        CUI_TRY(cudaMemcpy(tmp.data(), b->d_trig, sizeof(cui_trigger) * have, cudaMemcpyDeviceToHost), "trigger copy");
+    }
     std::sort(tmp.begin(), tmp.end(), [](const cui_trigger &x, const cui_trigger &y) {
         return x.tmpl != y.tmpl ? x.tmpl < y.tmpl : x.sample < y.sample;
     });
     const int64_t nout = std::min<int64_t>(have, capacity);
-    if (nout) std::memcpy(host_out, tmp.data(), sizeof(cui_trigger) * nout);
+    if (nout) std::memcpy(trig_out, tmp.data(), sizeof(cui_trigger) * nout);
     if ((int64_t)cnt > b->trig_cap)
         return fail(CUI_ERR_OVERFLOW, "%llu triggers exceed the device buffer of %lld (only those were kept)", cnt,
                     (long long)b->trig_cap);
     if ((int64_t)cnt > capacity)
         return fail(CUI_ERR_OVERFLOW, "%llu triggers exceed capacity %lld", cnt, (long long)capacity);
     return CUI_OK;
+}
+
+extern "C" cui_status cui_peaks(cui_bank b, cui_peak *host_out, int64_t count)
+{
+    if (!b || !host_out) return fail(CUI_ERR_ARG, "bank and host_out must be non-NULL");
+    if (count < 0 || count > b->nt) return fail(CUI_ERR_ARG, "count must be in [0, n_templates]");
+    if (!b->have_peaks) return fail(CUI_ERR_STATE, "no filter call kept its peaks in the handle");
+    return read_results(b, host_out, count, nullptr, 0, nullptr);
+}
+
+extern "C" cui_status cui_triggers(cui_bank b, cui_trigger *host_out, int64_t capacity, int64_t *n_total)
+{
+    if (!b || !n_total) return fail(CUI_ERR_ARG, "bank and n_total must be non-NULL");
+    if (capacity < 0 || (capacity > 0 && !host_out)) return fail(CUI_ERR_ARG, "bad capacity / host_out");
+    return read_results(b, nullptr, 0, host_out, capacity, n_total);
+}
+
+extern "C" cui_status cui_results(cui_bank b, cui_peak *host_peaks, int64_t n_peaks, cui_trigger *host_trig,
+                                  int64_t capacity, int64_t *n_total)
+{
+    if (!b || !host_peaks || !n_total) return fail(CUI_ERR_ARG, "bank, host_peaks and n_total must be non-NULL");
+    if (n_peaks < 0 || n_peaks > b->nt) return fail(CUI_ERR_ARG, "n_peaks must be in [0, n_templates]");
+    if (capacity < 0 || (capacity > 0 && !host_trig)) return fail(CUI_ERR_ARG, "bad capacity / host_trig");
+    if (!b->have_peaks) return fail(CUI_ERR_STATE, "no filter call kept its peaks in the handle");
+    return read_results(b, host_peaks, n_peaks, host_trig, capacity, n_total);
 }
 
 extern "C" cui_status cui_cluster_triggers(cui_bank b, cui_trigger *host_out, int64_t capacity, int64_t *n_total)
