@@ -561,7 +561,9 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e = {"value": w.n_templates * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": w.n * 8 + (w.n // 2 + 1) * 8,
-           "d2h_bytes_per_step": w.n_templates * 16 + n_trig * 24 + 8}
+           # peaks, the count, and the trigger prefix the read-out stages (at least 1024 records,
+           # twice the previous count; the count is the same every step here)
+           "d2h_bytes_per_step": w.n_templates * 16 + 8 + min(1 << 20, max(1024, 2 * n_trig)) * 24}
     bank2.close()
 
     # the plain per-template FP32 path on a subset of the bank, same segment

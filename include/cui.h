@@ -150,8 +150,10 @@ cui_status cui_triggers(cui_bank bank, cui_trigger *host_out, int64_t capacity, 
 
 /* cui_peaks and cui_triggers in one call: host_peaks[0 .. n_peaks) and up to
  * `capacity` trigger records with their total in *n_total, as those two calls
- * give them, read back with one synchronisation when the trigger count is at
- * most twice the previous call's (a larger count costs a second copy).
+ * give them, read back with one synchronisation: the copy of the peaks and the
+ * count goes with a copy of the first max(1024, 2 c) device trigger records
+ * (at most the device capacity), c the count of the handle's previous read-out
+ * (1024 before the first); a larger count costs a second copy of all records.
  * Synchronises.  Errors: as cui_peaks and cui_triggers.
  * Paper: the per-template maxima and candidate set of step 4, read back to the
  * host as the pipeline's result. */
