@@ -1,6 +1,7 @@
 """Comparison of the library's outputs with the oracle's (test helper).
 
-Rules (the survey's c8 reading of "trigger times bit-exact"):
+Rules (how "trigger times bit-exact" is read when two samples of a window
+hold nearly equal rho in FP64, so that FP32 rounding may pick either):
 * a sample index must match exactly unless the oracle's best and runner-up
   rho in that window (or over the valid range, for the peak) are within
   AMBIG relative; then any sample within that band is accepted and the case

@@ -20,7 +20,7 @@ def _oracle():
 
 
 def test_band_bins_match_the_oracle_band_edges():
-    # the oracle's template support is [k_low, k_hi) (band edges, reading c5)
+    # the oracle's template support is [k_low, k_hi) (the bins with f_low <= f_k < f_ISCO, below n/2)
     rng = np.random.default_rng(3)
     for n, f_low in [(1 << 12, 30.0), (1 << 14, 20.0), (1 << 16, 40.0)]:
         for _ in range(6):
