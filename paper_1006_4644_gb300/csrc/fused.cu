@@ -399,11 +399,9 @@ template <int R, typename E> __device__ __forceinline__ void p2_tw_table(E *u, i
     for (int r = 1; r < R; ++r) u[r] = cmul(u[r], t[r * NS]);
 }
 
-// the same by powers of one accurately computed root
-template <int R, typename E> __device__ __forceinline__ void p2_tw_pow(E *u, int j, int NS)
+// the same by powers of one accurately computed root w = exp(2 pi i jm / (NS R))
+template <int R, typename E> __device__ __forceinline__ void p2_tw_root(E *u, float2 w)
 {
-    const int jm = j & (NS - 1);
-    const float2 w = turn((unsigned)jm, (unsigned)(NS * R));
     float2 wr = w;
 #pragma unroll
     for (int r = 1; r < R; ++r) {
@@ -412,8 +410,15 @@ template <int R, typename E> __device__ __forceinline__ void p2_tw_pow(E *u, int
     }
 }
 
+template <int R> __device__ __forceinline__ float2 p2_root(int j, int NS)
+{
+    return turn((unsigned)(j & (NS - 1)), (unsigned)(NS * R));
+}
+
+// One stage: twiddles from the table `tw` (TABLE), else by powers of the
+// roots w[i] that the caller computed ahead (p2_root).
 template <int L, int R, int NS, bool TABLE, int PPT, typename E>
-__device__ __forceinline__ void p2_stage(E *v, E *row, int lt, const float2 *tw)
+__device__ __forceinline__ void p2_stage(E *v, E *row, int lt, const float2 *tw, const float2 *w = nullptr)
 {
     constexpr int TPR = L / PPT, T = PPT / R;
     p2_load<L, R, PPT>(v, row, lt);
@@ -421,7 +426,7 @@ __device__ __forceinline__ void p2_stage(E *v, E *row, int lt, const float2 *tw)
     for (int i = 0; i < T; ++i) {
         const int j = lt + i * TPR;
         if constexpr (TABLE) p2_tw_table<R>(v + i * R, j, NS, tw);
-        else p2_tw_pow<R>(v + i * R, j, NS);
+        else p2_tw_root<R>(v + i * R, w[i]);
         dft<R, +1>(v + i * R);
     }
 }
@@ -514,22 +519,28 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
     const int c = blockIdx.x * RPC + rr;
     E *row = sm + rr * LP;
     const char *yslice = (const char *)p.ywork + (size_t)y * (size_t)p.n * sizeof(ST);
-    // tw1[r R0 + jm] = exp(2 pi i jm r / (R0 R1))
-    for (int m = tid; m < R0 * R1; m += NT) tw1[m] = turn((m % R0) * (m / R0), R0 * R1);
-    if constexpr (R3 > 1)
-        for (int m = tid; m < R0 * R1 * R2; m += NT)
-            tw2[m] = turn((m % (R0 * R1)) * (m / (R0 * R1)), R0 * R1 * R2);
-
+    // roots of the last stage's twiddles, when they are not taken from tw1
+    float2 wl[R2 == 1 ? 1 : PPT / RL];
+    if constexpr (R2 != 1)
+#pragma unroll
+        for (int i = 0; i < PPT / RL; ++i) wl[i] = p2_root<RL>(lg + i * TPR, NSL);
     E v[PPT];
     {
         constexpr int T = PPT / R0;
+        // every load of Y is issued before the twiddle tables are filled, so
+        // that their latency overlaps the table arithmetic
 #pragma unroll
-        for (int i = 0; i < T; ++i) {
-            const int j = lt + i * TPR;
+        for (int i = 0; i < T; ++i)
 #pragma unroll
-            for (int r = 0; r < R0; ++r) v[i * R0 + r] = ld_y<ST, PAIR>(yslice, (size_t)c * L + j + r * (L / R0));
-            dft<R0, +1>(v + i * R0);
-        }
+            for (int r = 0; r < R0; ++r)
+                v[i * R0 + r] = ld_y<ST, PAIR>(yslice, (size_t)c * L + lt + i * TPR + r * (L / R0));
+        // tw1[r R0 + jm] = exp(2 pi i jm r / (R0 R1))
+        for (int m = tid; m < R0 * R1; m += NT) tw1[m] = turn((m % R0) * (m / R0), R0 * R1);
+        if constexpr (R3 > 1)
+            for (int m = tid; m < R0 * R1 * R2; m += NT)
+                tw2[m] = turn((m % (R0 * R1)) * (m / (R0 * R1)), R0 * R1 * R2);
+#pragma unroll
+        for (int i = 0; i < T; ++i) dft<R0, +1>(v + i * R0);
         p2_store<L, R0, 1, PPT>(v, row, lt);
         __syncthreads();
     }
@@ -563,7 +574,7 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
             __syncthreads();
         }
     }
-    p2_stage<L, RL, NSL, R2 == 1, PPT>(v, row, lg, tw1);
+    p2_stage<L, RL, NSL, R2 == 1, PPT>(v, row, lg, tw1, wl);
 
     // Epilogue.  Output d of lane l is sample s = c_l + n1 d with
     // c_l = c + l n1/2; |z|^2 is compared before the (positive) scaling.  The
