@@ -275,13 +275,18 @@ __global__ void __launch_bounds__(C *N1 / 16, p1_min_blocks(C *N1 / 16)) k_pass1
     }
     for (int m = tid; m < ng * kNB; m += NT) // a CTA can have fewer threads than G kNB
         cdf[m / kNB][m % kNB] = p.coef_df[(int64_t)p.order[p.base + y0 + m / kNB] * kNB + m % kNB];
+    // band edges of the CTA's templates, read once
+    __shared__ int2 tk[G];
+    for (int g = tid; g < ng; g += NT) {
+        const int t = p.order[p.base + y0 + g];
+        tk[g] = make_int2(p.khi[t], p.kex[t]);
+    }
     __syncthreads();
 
     for (int g = 0; g < ng; ++g) {
         const int y = y0 + g;
-        const int t = p.order[p.base + y];
-        const int khi = p.khi[t];
-        const int kex = p.kex[t];
+        const int khi = tk[g].x;
+        const int kex = tk[g].y;
         const int a_hi = min(NROW, ceil_div_pos(khi - b0, n2));
 
         float2 v[16];
