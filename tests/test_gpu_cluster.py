@@ -1,7 +1,7 @@
 """Cross-template trigger clustering on the GPU (cui_cluster_triggers): the
 device result equals the oracle's clustering of the device's own triggers bit
-for bit, matches the oracle's clustering of its own FP64 triggers (c8 rule for
-near-ties), and stays exact through a trigger-buffer overflow, template
+for bit, matches the oracle's clustering of its own FP64 triggers (near-ties
+as in parity.py), and stays exact through a trigger-buffer overflow, template
 subsets and the per-template path."""
 
 import numpy as np
