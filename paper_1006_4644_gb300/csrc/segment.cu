@@ -298,6 +298,7 @@ __global__ void k_wmax(const double2 *__restrict__ X, const double *__restrict__
                        int64_t nh, int k_low, int e_fs, SegScales *sc)
 {
     constexpr int kNone = -(1 << 20);
+    __shared__ int s_ew[32], s_ed[32];
     int ew = kNone, ed = kNone;
     for (int64_t k = k_low + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nh;
          k += (int64_t)gridDim.x * blockDim.x) {
@@ -315,10 +316,24 @@ __global__ void k_wmax(const double2 *__restrict__ X, const double *__restrict__
         ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, o));
         ed = max(ed, __shfl_xor_sync(0xffffffffu, ed, o));
     }
-    if ((threadIdx.x & 31) == 0 && ed != kNone) {
-        const double mw = ldexp(1.0, ew + e_fs), md = ldexp(1.0, ed + e_fs);
-        atomicMax((unsigned long long *)&sc->max_w, (unsigned long long)__double_as_longlong(mw));
-        atomicMax((unsigned long long *)&sc->max_d, (unsigned long long)__double_as_longlong(md));
+    // then over the block's warps, so that one atomic pair per block (not per
+    // warp) reaches the two shared addresses
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_ew[wid] = ew;
+        s_ed[wid] = ed;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            ew = max(ew, s_ew[w]);
+            ed = max(ed, s_ed[w]);
+        }
+        if (ed != kNone) {
+            const double mw = ldexp(1.0, ew + e_fs), md = ldexp(1.0, ed + e_fs);
+            atomicMax((unsigned long long *)&sc->max_w, (unsigned long long)__double_as_longlong(mw));
+            atomicMax((unsigned long long *)&sc->max_d, (unsigned long long)__double_as_longlong(md));
+        }
     }
 }
 
