@@ -383,6 +383,20 @@ cui_status cui_prescreen_gradient(cui_prescreen p, const float *feat_dev, const 
 cui_status cui_prescreen_get_state(cui_prescreen p, float *theta, float *m, float *v, int64_t *step);
 cui_status cui_prescreen_set_state(cui_prescreen p, const float *theta, const float *m, const float *v,
                                    int64_t step);
+/* Filtering order from region scores, on host arrays: the n_templates bank
+ * points (m1[t], m2[t] in solar masses, finite and > 0) sorted by chirp mass
+ * Mc = (m1 m2)^(3/5) / (m1 + m2)^(1/5) (equal Mc: lower index first) and cut
+ * into `regions` equal-count groups in increasing Mc (the first
+ * n_templates mod regions groups one template longer); then the groups by
+ * descending scores[0 .. regions) (finite; equal scores: lower region first),
+ * the first min(top_k, regions) of them, each in increasing Mc.  Writes those
+ * template indices to order_out (room for n_templates, caller-owned) and
+ * their number to *n_out: the `order` argument of cui_filter_bank.  Does not
+ * touch the GPU.  Errors: CUI_ERR_ARG.  Paper: the introduction's remark that
+ * at the ET scale of 1-2 million templates a search should be smarter than
+ * brute force; the regions and scores are this library's prescreen. */
+cui_status cui_prescreen_rank(const double *m1, const double *m2, int64_t n_templates, const float *scores,
+                              int32_t regions, int32_t top_k, int32_t *order_out, int64_t *n_out);
 
 /* Allocation-free normalisation: sigma_t^2 = 4 df sum_k |h~_k|^2 / S_k of
  * `count` templates (m1[t], m2[t], host arrays) for the one-sided PSD psd_dev

@@ -22,8 +22,8 @@ from . import _lib
 from ._lib import (CUI_PLAIN, CUI_PLAIN_FP64, CUI_PSI_FP64, CUI_STORE_BF16, PEAK_DTYPE, TRIGGER_DTYPE, CuiError,
                    cui_bank_desc)
 
-__all__ = ["Bank", "Prescreen", "CuiError", "CUI_PSI_FP64", "CUI_STORE_BF16", "CUI_PLAIN", "CUI_PLAIN_FP64", "PEAK_DTYPE",
-           "TRIGGER_DTYPE", "load"]
+__all__ = ["Bank", "Prescreen", "prescreen_rank", "CuiError", "CUI_PSI_FP64", "CUI_STORE_BF16", "CUI_PLAIN",
+           "CUI_PLAIN_FP64", "PEAK_DTYPE", "TRIGGER_DTYPE", "load"]
 
 load = _lib.load
 
@@ -247,6 +247,25 @@ class Bank:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def prescreen_rank(m1, m2, scores, top_k: int | None = None):
+    """Template order for ``Bank.filter``: the chirp-mass regions of the bank
+    (as many as ``scores`` has entries) by descending score, the first
+    ``top_k`` of them (all by default) (cui_prescreen_rank)."""
+    m1 = np.ascontiguousarray(m1, dtype=np.float64)
+    m2 = np.ascontiguousarray(m2, dtype=np.float64)
+    sc = np.ascontiguousarray(scores, dtype=np.float32).reshape(-1)
+    if m1.shape != m2.shape or m1.ndim != 1:
+        raise ValueError("m1 and m2 must be 1-D arrays of one length")
+    regions = len(sc)
+    k = regions if top_k is None else int(top_k)
+    out = np.empty(max(len(m1), 1), dtype=np.int32)
+    cnt = C.c_int64()
+    lib = _lib.load_prescreen(_lib.load())
+    _lib.check(lib.cui_prescreen_rank(m1.ctypes.data, m2.ctypes.data, len(m1), sc.ctypes.data, regions, k,
+                                      out.ctypes.data, C.byref(cnt)), "cui_prescreen_rank")
+    return out[: cnt.value].copy()
 
 
 class Prescreen:

@@ -128,8 +128,9 @@ def load_prescreen(lib):
     lib.cui_prescreen_gradient.argtypes = [vp, vp, vp, C.c_int64, vp, C.POINTER(C.c_float)]
     lib.cui_prescreen_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_int64)]
     lib.cui_prescreen_set_state.argtypes = [vp, vp, vp, vp, C.c_int64]
+    lib.cui_prescreen_rank.argtypes = [vp, vp, C.c_int64, vp, C.c_int32, C.c_int32, vp, C.POINTER(C.c_int64)]
     for name in ("cui_prescreen_create", "cui_prescreen_info", "cui_prescreen_features", "cui_prescreen_bank_features",
                  "cui_prescreen_scores", "cui_prescreen_train_step", "cui_prescreen_gradient",
-                 "cui_prescreen_get_state", "cui_prescreen_set_state"):
+                 "cui_prescreen_get_state", "cui_prescreen_set_state", "cui_prescreen_rank"):
         getattr(lib, name).restype = C.c_int
     return lib

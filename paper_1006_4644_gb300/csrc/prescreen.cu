@@ -676,3 +676,42 @@ extern "C" cui_status cui_prescreen_set_state(cui_prescreen p, const float *thet
     PS_TRY(cudaStreamSynchronize(p->stream));
     return CUI_OK;
 }
+
+// ------------------------------------------------------------ ranking ---
+// Host work on O(templates) values: the bank in increasing chirp mass
+// (stable, so equal masses keep bank order), cut into `regions` equal-count
+// groups (the first n mod regions one template longer), the groups taken by
+// descending score (equal scores: lower region first).
+extern "C" cui_status cui_prescreen_rank(const double *m1, const double *m2, int64_t n_templates, const float *scores,
+                                         int32_t regions, int32_t top_k, int32_t *order_out, int64_t *n_out)
+{
+    if (!m1 || !m2 || !scores || !n_out) return ps_fail(CUI_ERR_ARG, "m1, m2, scores and n_out must be non-NULL");
+    if (n_templates < 0 || n_templates > INT32_MAX) return ps_fail(CUI_ERR_ARG, "n_templates must be in [0, 2^31)");
+    if (n_templates > 0 && !order_out) return ps_fail(CUI_ERR_ARG, "order_out must be non-NULL");
+    if (regions < 1) return ps_fail(CUI_ERR_ARG, "regions must be >= 1");
+    if (top_k < 0) return ps_fail(CUI_ERR_ARG, "top_k must be >= 0");
+    const int64_t n = n_templates;
+    std::vector<double> mc((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(m1[i] > 0.0 && m2[i] > 0.0 && std::isfinite(m1[i]) && std::isfinite(m2[i])))
+            return ps_fail(CUI_ERR_ARG, "masses must be finite and > 0");
+        mc[(size_t)i] = std::pow(m1[i] * m2[i], 0.6) / std::pow(m1[i] + m2[i], 0.2);
+    }
+    for (int32_t r = 0; r < regions; ++r)
+        if (!std::isfinite(scores[r])) return ps_fail(CUI_ERR_ARG, "scores must be finite");
+    std::vector<int32_t> by_mc((size_t)n);
+    for (int64_t i = 0; i < n; ++i) by_mc[(size_t)i] = (int32_t)i;
+    std::stable_sort(by_mc.begin(), by_mc.end(), [&](int32_t a, int32_t b) { return mc[(size_t)a] < mc[(size_t)b]; });
+    std::vector<int32_t> ranked((size_t)regions);
+    for (int32_t r = 0; r < regions; ++r) ranked[(size_t)r] = r;
+    std::stable_sort(ranked.begin(), ranked.end(), [&](int32_t a, int32_t b) { return scores[a] > scores[b]; });
+    const int64_t q = n / regions, rem = n % regions;
+    auto start = [&](int64_t r) { return r * q + std::min<int64_t>(r, rem); };
+    int64_t w = 0;
+    for (int32_t k = 0; k < std::min(top_k, regions); ++k) {
+        const int64_t r = ranked[(size_t)k];
+        for (int64_t p = start(r); p < start(r + 1); ++p) order_out[w++] = by_mc[(size_t)p];
+    }
+    *n_out = w;
+    return CUI_OK;
+}

@@ -59,8 +59,7 @@ def main():
 
     import torch
 
-    from paper_1006_4644_gb300 import Bank, Prescreen, build
-    from paper_1006_4644_gb300.regions import ranked_order
+    from paper_1006_4644_gb300 import Bank, Prescreen, build, prescreen_rank
 
     build.build()
     n, fs, f_low, R, W = 1 << 16, 4096.0, 20.0, 100, 4096
@@ -188,7 +187,7 @@ def main():
                 p.bank_features(bank, feat1)
                 feat_n = ((feat1 - mu) / sd).contiguous()
                 score(feat_n, sc1)
-                order = ranked_order(sc1.cpu().numpy()[0], groups, k_star)
+                order = prescreen_rank(m1, m2, sc1.cpu().numpy()[0], k_star)
                 bank.filter(order)
                 ev[2].record(stream)
                 torch.cuda.synchronize()
@@ -199,7 +198,7 @@ def main():
             rep["speedup"] = t_ex / t_ps
             # the same timing at the 99 % and 95 % points (misses allowed)
             for q in (99, 95):
-                order = ranked_order(np.zeros(R), groups, rep[f"K_{q}pct"])
+                order = prescreen_rank(m1, m2, np.zeros(R), rep[f"K_{q}pct"])
                 bank.upload(synth.strain_from_spectrum(dte[0], n, fs), psd)
                 torch.cuda.synchronize()
                 ev[0].record(stream)
