@@ -135,7 +135,8 @@ cui_status cui_filter_bank(cui_bank bank, const int32_t *order, int64_t count, c
 /* Copy the peaks of the last filter call that kept them in the handle to
  * host_out[0 .. count), indexed by template (count <= n_templates).
  * Synchronises.  Errors: CUI_ERR_ARG, CUI_ERR_STATE, CUI_ERR_CUDA,
- * CUI_ERR_TIMEOUT. */
+ * CUI_ERR_TIMEOUT.  Paper: each template's maximum of the SNR over the data
+ * chunk, step 4 of Sec. "Matched filtering". */
 cui_status cui_peaks(cui_bank bank, cui_peak *host_out, int64_t count);
 
 /* Copy the triggers of the last filter call to host_out and their exact total
@@ -290,7 +291,8 @@ typedef struct {
     int32_t batch; /* templates per launch pair, >= 1 */
 } cui_tuning;
 
-/* Current tiling.  Errors: CUI_ERR_ARG, CUI_ERR_STATE (per-template path). */
+/* Current tiling.  Errors: CUI_ERR_ARG, CUI_ERR_STATE (per-template path).
+ * Not in the paper (this library's kernel tiling), as the two calls below. */
 cui_status cui_bank_get_tuning(cui_bank bank, cui_tuning *out);
 
 /* Select a tiling; reallocates the workspace (synchronises the stream).
@@ -341,6 +343,10 @@ cui_status cui_trace_read(cui_bank bank, cui_trace_stat *host_out, int64_t capac
  * label cross-entropy; Adam.  Training is deterministic for a given seed.
  * Device arrays: features [count][bands][N/frame] float, targets and scores
  * [count][regions] float.  Asynchronous on desc.stream unless stated.
+ * Errors of every call below: CUI_ERR_ARG (NULL handle or pointer, a size
+ * out of the ranges stated, a count above max_batch), CUI_ERR_OOM (create),
+ * CUI_ERR_CUDA; cui_prescreen_bank_features also CUI_ERR_STATE (the bank
+ * holds no segment).
  * ------------------------------------------------------------------------ */
 typedef struct cui_prescreen_s *cui_prescreen;
 
@@ -424,7 +430,9 @@ cui_status cui_template_sigma_noalloc(const double *psd_dev, int64_t n, double s
  * NULL is allowed. */
 void cui_bank_destroy(cui_bank bank);
 
-/* Message of the last failing call on this thread ("" if none). */
+/* Message of the last failing call on this thread ("" if none); the string
+ * belongs to the library and stays valid until the thread's next failing
+ * call.  Not in the paper. */
 const char *cui_last_error(void);
 
 #ifdef __cplusplus
