@@ -416,6 +416,8 @@ def main():
     ap.add_argument("--flags", type=int, default=0, help="extra CUI_* flags for the fused path")
     ap.add_argument("--plain-templates", type=int, default=64)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false",
+                    help="skip the end-to-end leg (a smaller process for profiler captures)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--tuning", default=None, help="fixed tiling n1,ccols,rpc,batch (skips the autotuner)")
     ap.add_argument("--extras", action="store_true",
@@ -539,53 +541,13 @@ def main():
                              "peak_basis": "152 SMs x 128 FP32 lanes x 2.07 GHz, one add per lane per clock"}
 
     # end to end through the public API with pinned host buffers
-    strain_h = torch.from_numpy(strain).pin_memory()
-    psd_h = torch.from_numpy(psd_fin).pin_memory()
-    e2e_steps = max(3, args.steps // 2)
-    bank2 = Bank(m1, m2, n=w.n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, flags=args.flags, stream=stream.cuda_stream)
-    bank2.set_tuning(**tuning)
-    n_trig = 0
+    e2e = None
+    if args.e2e:
+        e2e = e2e_leg(w, m1, m2, strain, psd_fin, tuning, args, stream)
 
-    def e2e_step():
-        nonlocal n_trig
-        bank2.upload(strain_h.numpy(), psd_h.numpy())
-        bank2.filter()
-        _, tr, n_trig = bank2.results()
-
-    e2e_step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": w.n_templates * e2e_steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": w.n * 8 + (w.n // 2 + 1) * 8,
-           # peaks, the count, and the trigger prefix the read-out stages (at least 1024 records,
-           # twice the previous count; the count is the same every step here)
-           "d2h_bytes_per_step": w.n_templates * 16 + 8 + min(1 << 20, max(1024, 2 * n_trig)) * 24}
-    bank2.close()
-
-    # the plain per-template FP32 path on a subset of the bank, same segment
     plain = None
     if args.plain_templates > 0:
-        npl = min(args.plain_templates, w.n_templates)
-        pb = Bank(m1, m2, n=w.n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, flags=CUI_PLAIN, stream=stream.cuda_stream)
-        pb.upload(strain_d, psd_d)
-        order = np.arange(npl)
-        pb.filter(order)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        reps = 3
-        for _ in range(reps):
-            pb.upload(strain_d, psd_d)
-            pb.filter(order)
-        b.record(stream)
-        torch.cuda.synchronize()
-        pv = npl * reps / (a.elapsed_time(b) / 1e3)
-        plain = {"value": pv, "unit": UNIT, "templates": npl, "mixed_over_plain": value / pv}
-        pb.close()
+        plain = plain_leg(w, m1, m2, strain_d, psd_d, args, stream, value)
 
     cpu, acc = None, None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -614,6 +576,69 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def e2e_leg(w, m1, m2, strain, psd_fin, tuning, args, stream):
+    """The same metric end to end through the public API: every step uploads
+    the strain and PSD from pinned host memory and reads peaks and triggers
+    back (cui_results)."""
+    import torch
+
+    from paper_1006_4644_gb300 import Bank
+
+    strain_h = torch.from_numpy(strain).pin_memory()
+    psd_h = torch.from_numpy(psd_fin).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+    bank2 = Bank(m1, m2, n=w.n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, flags=args.flags, stream=stream.cuda_stream)
+    bank2.set_tuning(**tuning)
+    n_trig = 0
+
+    def e2e_step():
+        nonlocal n_trig
+        bank2.upload(strain_h.numpy(), psd_h.numpy())
+        bank2.filter()
+        _, tr, n_trig = bank2.results()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": w.n_templates * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": w.n * 8 + (w.n // 2 + 1) * 8,
+           # peaks, the count, and the trigger prefix the read-out stages (at least 1024 records,
+           # twice the previous count; the count is the same every step here)
+           "d2h_bytes_per_step": w.n_templates * 16 + 8 + min(1 << 20, max(1024, 2 * n_trig)) * 24}
+    bank2.close()
+    return e2e
+
+
+def plain_leg(w, m1, m2, strain_d, psd_d, args, stream, value):
+    """The plain per-template FP32 path on a subset of the bank, same segment."""
+    import numpy as np
+    import torch
+
+    from paper_1006_4644_gb300 import CUI_PLAIN, Bank
+
+    npl = min(args.plain_templates, w.n_templates)
+    pb = Bank(m1, m2, n=w.n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, flags=CUI_PLAIN, stream=stream.cuda_stream)
+    pb.upload(strain_d, psd_d)
+    order = np.arange(npl)
+    pb.filter(order)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    reps = 3
+    for _ in range(reps):
+        pb.upload(strain_d, psd_d)
+        pb.filter(order)
+    b.record(stream)
+    torch.cuda.synchronize()
+    pv = npl * reps / (a.elapsed_time(b) / 1e3)
+    pb.close()
+    return {"value": pv, "unit": UNIT, "templates": npl, "mixed_over_plain": value / pv}
 
 
 if __name__ == "__main__":

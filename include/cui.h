@@ -287,7 +287,9 @@ cui_status cui_bank_template(cui_bank bank, int64_t t, float *out_dev);
 typedef struct {
     int32_t n1;    /* 64, 128 or 256 (subject to the kernels built for N) */
     int32_t ccols; /* 16, 32 or 64 */
-    int32_t rpc;   /* rows per pass-2 CTA */
+    int32_t rpc;   /* rows per pass-2 CTA; 0: the streamed persistent pass 2
+                      (one CTA per SM, row pairs copied into shared memory by
+                      the bulk-copy engine), for n2 = N / n1 = 4096 */
     int32_t batch; /* templates per launch pair, >= 1 */
 } cui_tuning;
 
@@ -308,6 +310,23 @@ cui_status cui_bank_set_tuning(cui_bank bank, const cui_tuning *tuning);
  * CUI_ERR_STATE (no segment, or per-template path), CUI_ERR_ARG, CUI_ERR_CUDA.
  * Not in the paper: its kernels had no tunable tiling. */
 cui_status cui_bank_autotune(cui_bank bank, int32_t reps, cui_tuning *best, double *best_ms);
+
+/* Bounds of the handle's device waits, for tests of the error path.  The
+ * only spins in the library are the compare-and-swap loops that raise the
+ * peak, window and cluster slots (at most cas_rounds rounds, default 2^20)
+ * and, in the streamed pass 2 (tiling rpc 0), each team's wait for its row
+ * pair to land in shared memory (at most copy_wait_ns ns on the GPU's global
+ * timer, default 10^9; 0 makes every such wait give up at once).  A wait
+ * that runs out sets the device error word and
+ * its kernel skips the rest of its work (the streamed pass 2 still waits up to
+ * 10^9 ns for a copy in flight before its CTA exits); the next synchronising
+ * call returns CUI_ERR_TIMEOUT and clears the word, and the handle stays
+ * usable: the next cui_segment_upload and filter call give full results
+ * again.  Negative values restore the defaults; values above them return
+ * CUI_ERR_ARG.  Synchronises the stream.  Paper: the final reduction of the
+ * per-template maxima (Sec. "Matched filtering"), whose device-side form here
+ * needs these waits; the bounds themselves are not in the paper. */
+cui_status cui_bank_set_wait_bounds(cui_bank bank, int64_t cas_rounds, int64_t copy_wait_ns);
 
 /* Tracing.  cui_trace_enable(bank, level): 0 off; 1 records CUDA events on
  * desc.stream around each call's groups of kernels ("segment", "plain", and
@@ -405,22 +424,26 @@ cui_status cui_prescreen_rank(const double *m1, const double *m2, int64_t n_temp
                               int32_t regions, int32_t top_k, int32_t *order_out, int64_t *n_out);
 
 /* Allocation-free normalisation: sigma_t^2 = 4 df sum_k |h~_k|^2 / S_k of
- * `count` templates (m1[t], m2[t], host arrays) for the one-sided PSD psd_dev
- * (N/2 + 1 FP64 values in device memory, read on [k_lo, N/2)), written to
- * sigma2_dev[0 .. count) (device, caller-owned), asynchronously on `stream`.
- * No counterpart in the paper: it serves callers that cannot allocate device
- * memory when they need the result -- work being captured into a CUDA graph,
- * pipelines whose device memory belongs to one pool allocator, real-time
- * loops that cannot wait for an allocation -- for instance to renormalise a
- * bank after a new PSD estimate.  It allocates nothing: its scratch is one
- * array of about 8.2 MiB compiled into the library, which every GPU that
- * loads the library holds until the process exits.  The first call on a
- * device looks up that array's device address (with the device current);
- * make that first call before any stream capture.  Limits: N a power of two
- * in [64, 2^20], 1 <= count <= 16384; larger values return CUI_ERR_ARG.  All
- * calls share the array: calls that overlap on the GPU (other streams, other
- * host threads) race and must be serialised by the caller.  Same conventions
- * and units as cui_bank_create; k_lo = ceil(f_low / df), k_hi as there.
+ * `count` templates (m1[t], m2[t], host arrays, read during the call) for the
+ * one-sided PSD psd_dev (N/2 + 1 FP64 values in device memory, read on
+ * [k_lo, N/2)), written to sigma2_dev[0 .. count) (device, caller-owned),
+ * asynchronously on `stream`.  No counterpart in the paper: it serves callers
+ * that cannot allocate device memory when they need the result -- pipelines
+ * whose device memory belongs to one pool allocator with a fixed budget,
+ * real-time loops that cannot wait for an allocation -- for instance to
+ * renormalise a bank after a new PSD estimate.  It allocates nothing: its
+ * scratch is one array of about 8.2 MiB compiled into the library, which
+ * every GPU that loads the library holds until the process exits.  The first
+ * call on a device looks up that array's device address (with the device
+ * current); make that first call before any stream capture.  The upper bins
+ * are computed on the host and copied from pageable host memory (staged
+ * before the call returns).  psd_dev is not validated: it must be finite and
+ * > 0 on [k_lo, N/2), or sigma^2 comes out inf or NaN with CUI_OK.  Limits: N
+ * a power of two in [64, 2^20], 1 <= count <= 16384; larger values return
+ * CUI_ERR_ARG.  All calls share the array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Same conventions and units as cui_bank_create;
+ * k_lo = ceil(f_low / df) (capped at N/2), k_hi as there.
  * Errors: CUI_ERR_ARG, CUI_ERR_CUDA. */
 cui_status cui_template_sigma_noalloc(const double *psd_dev, int64_t n, double sample_rate, double f_low,
                                       const double *m1, const double *m2, int64_t count, double *sigma2_dev,

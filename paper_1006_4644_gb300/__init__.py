@@ -211,6 +211,12 @@ class Bank:
         tu = _lib.cui_tuning(int(n1), int(ccols), int(rpc), int(batch))
         _lib.check(self._l.cui_bank_set_tuning(self._h, C.byref(tu)), "cui_bank_set_tuning")
 
+    def set_wait_bounds(self, cas_rounds: int = -1, copy_wait_ns: int = -1):
+        """Lower the bounds of the device waits (for tests of the error path);
+        negative values restore the defaults."""
+        _lib.check(self._l.cui_bank_set_wait_bounds(self._h, int(cas_rounds), int(copy_wait_ns)),
+                   "cui_bank_set_wait_bounds")
+
     def autotune(self, reps: int = 2):
         """Time every tiling with kernels at this N on the uploaded segment,
         keep the fastest; returns (tiling, ms per filter call)."""

@@ -78,6 +78,7 @@ def load():
     lib.cui_bank_get_tuning.argtypes = [vp, C.POINTER(cui_tuning)]
     lib.cui_bank_set_tuning.argtypes = [vp, C.POINTER(cui_tuning)]
     lib.cui_bank_autotune.argtypes = [vp, C.c_int32, C.POINTER(cui_tuning), C.POINTER(C.c_double)]
+    lib.cui_bank_set_wait_bounds.argtypes = [vp, C.c_int64, C.c_int64]
     lib.cui_template_sigma_noalloc.argtypes = [vp, C.c_int64, C.c_double, C.c_double, vp, vp, C.c_int64, vp, vp]
     lib.cui_template_sigma_noalloc.restype = C.c_int
     lib.cui_trace_enable.argtypes = [vp, C.c_int]
@@ -89,7 +90,7 @@ def load():
                  "cui_cluster_triggers", "cui_trigger_chisq", "cui_td_template", "cui_bank_set_band",
                  "cui_band_correlate", "cui_segment_band_series", "cui_results",
                  "cui_bank_sigma", "cui_bank_template", "cui_trace_enable", "cui_trace_read",
-                 "cui_bank_get_tuning", "cui_bank_set_tuning", "cui_bank_autotune"):
+                 "cui_bank_get_tuning", "cui_bank_set_tuning", "cui_bank_autotune", "cui_bank_set_wait_bounds"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib

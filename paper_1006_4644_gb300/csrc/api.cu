@@ -203,6 +203,8 @@ struct cui_bank_s {
     Slot *d_pwin = nullptr;
     Slot *d_cluster = nullptr; // [nwin] loudest trigger of each window over the bank (last filter call)
     bool filtered = false;     // a filter call ran since the last upload
+    int cas_rounds = kCasRounds;                // bounds of the device waits
+    unsigned long long copy_wait_ns = kCopyWaitNs;
     // outputs
     cui_trigger *d_trig = nullptr;
     int64_t trig_cap = 0;
@@ -429,7 +431,8 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     b->log2n = ilog2(d.n);
     b->nt = n_templates;
     b->df = d.sample_rate / (double)d.n;
-    b->k_low = std::max<int>(1, (int)std::ceil(d.f_low / b->df));
+    // clamped before the conversion: an f_low at or above Nyquist leaves every band empty
+    b->k_low = std::max<int>(1, (int)std::min<double>(std::ceil(d.f_low / b->df), (double)b->nh));
     b->band_lo = b->k_low;
     b->band_hi = (int)(d.n / 2);
     b->fused = !(d.flags & CUI_PLAIN) && fused_supported(b->log2n);
@@ -627,6 +630,8 @@ static FusedArgs fused_args(cui_bank b, const int32_t *order, int64_t base)
     a.peak = b->d_peak;
     a.win = b->d_win;
     a.err = b->d_err;
+    a.cas_rounds = b->cas_rounds;
+    a.copy_wait_ns = b->copy_wait_ns;
     a.n = b->n;
     a.log2n = b->log2n;
     a.n1 = b->n1;
@@ -667,6 +672,7 @@ static FinalizeArgs finalize_args(cui_bank b, const int32_t *d_ord, cui_peak *po
     fa.trig_count = b->d_trig_count;
     fa.cluster = b->d_cluster;
     fa.err = b->d_err;
+    fa.cas_rounds = b->cas_rounds;
     fa.base = 0;
     fa.count = 0;
     return fa;
@@ -810,6 +816,7 @@ extern "C" cui_status cui_filter_bank(cui_bank b, const int32_t *order, int64_t 
         a.peak = b->d_peak;
         a.win = b->d_pwin;
         a.err = b->d_err;
+        a.cas_rounds = b->cas_rounds;
         a.n = b->n;
         a.log2n = b->log2n;
         a.pn_x2 = b->desc.pn_order_x2;
@@ -833,6 +840,22 @@ extern "C" cui_status cui_filter_bank(cui_bank b, const int32_t *order, int64_t 
     }
     b->have_peaks = peaks_dev == nullptr;
     b->filtered = true;
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_bank_set_wait_bounds(cui_bank b, int64_t cas_rounds, int64_t copy_wait_ns)
+{
+    if (!b) return fail(CUI_ERR_ARG, "bank is NULL");
+    if (cas_rounds > kCasRounds || copy_wait_ns > (int64_t)kCopyWaitNs)
+        return fail(CUI_ERR_ARG, "bounds above the defaults (%d rounds, %llu ns) are not allowed", kCasRounds,
+                    (unsigned long long)kCopyWaitNs);
+    CUI_TRY(cudaStreamSynchronize(b->stream), "stream synchronize");
+    b->cas_rounds = cas_rounds < 0 ? kCasRounds : (int)cas_rounds;
+    b->copy_wait_ns = copy_wait_ns < 0 ? kCopyWaitNs : (unsigned long long)copy_wait_ns;
+    if (b->gexec) { // the captured graph holds the previous bounds
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
     return CUI_OK;
 }
 
@@ -868,7 +891,7 @@ extern "C" cui_status cui_bank_autotune(cui_bank b, int32_t reps, cui_tuning *be
     CUI_TRY(cudaEventCreate(&e1), "autotune events");
     cui_tuning cur = {b->n1, b->ccols, b->rpc, b->batch}, top = cur;
     double top_ms = 1e300;
-    const int n1s[] = {64, 128, 256}, ccs[] = {16, 32, 64}, rpcs[] = {1, 2, 4, 8, 16, 32};
+    const int n1s[] = {64, 128, 256}, ccs[] = {16, 32, 64}, rpcs[] = {0, 1, 2, 4, 8, 16, 32};
     const int64_t per = b->n * ((b->desc.flags & CUI_STORE_BF16) ? 4 : 8);
     std::vector<int> batches;
     for (int64_t bt = 16; bt <= 4096; bt *= 4)

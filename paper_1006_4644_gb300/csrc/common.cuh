@@ -345,16 +345,22 @@ __device__ __forceinline__ unsigned long long make_key(float rho2, uint32_t samp
     return ((unsigned long long)__float_as_uint(rho2) << 32) | (unsigned long long)(0xFFFFFFFFu - sample);
 }
 
+// Rounds of the compare-and-swap loops below before they give up (the
+// library's default; a bank can lower it to test the error path).
+constexpr int kCasRounds = 1 << 20;
+// Time limit of a device wait for a bulk copy (global timer, ns).
+constexpr unsigned long long kCopyWaitNs = 1000000000ull;
+
 // Raise the slot to (key, phase) if key is larger.  Lock-free: each failed
 // CAS means another thread stored a larger key, so the loop ends after at most
-// as many rounds as there are competing writers; the bound only guards
-// against a logic error and is reported through *err.
-__device__ __forceinline__ void slot_max(Slot *s, unsigned long long key, float phase, int *err)
+// as many rounds as there are competing writers; the bound (`rounds`) only
+// guards against a logic error and is reported through *err.
+__device__ __forceinline__ void slot_max(Slot *s, unsigned long long key, float phase, int *err, int rounds)
 {
     unsigned long long cur_lo = *(volatile unsigned long long *)&s->key;
     unsigned long long cur_hi = *(volatile unsigned long long *)&s->phase_bits;
     const unsigned long long new_hi = (unsigned long long)__float_as_uint(phase);
-    for (int it = 0; it < (1 << 20); ++it) {
+    for (int it = 0; it < rounds; ++it) {
         if (cur_lo >= key) return;
         unsigned long long old_lo, old_hi;
         asm volatile("{\n\t.reg .b128 d, c, n;\n\t"
@@ -376,13 +382,13 @@ __device__ __forceinline__ void slot_max(Slot *s, unsigned long long key, float 
 // template) is larger; the template is kept as 0xFFFFFFFF - tmpl in `pad`, so
 // among equal keys the lowest template wins.  Same bounded CAS as slot_max.
 __device__ __forceinline__ void cluster_max(Slot *s, unsigned long long key, uint32_t tmpl, uint32_t phase_bits,
-                                            int *err)
+                                            int *err, int rounds)
 {
     const unsigned long long tinv = (unsigned long long)(0xFFFFFFFFu - tmpl);
     const unsigned long long new_hi = (tinv << 32) | (unsigned long long)phase_bits;
     unsigned long long cur_lo = *(volatile unsigned long long *)&s->key;
     unsigned long long cur_hi = *(volatile unsigned long long *)&s->phase_bits;
-    for (int it = 0; it < (1 << 20); ++it) {
+    for (int it = 0; it < rounds; ++it) {
         if (cur_lo > key || (cur_lo == key && (cur_hi >> 32) >= tinv)) return;
         unsigned long long old_lo, old_hi;
         asm volatile("{\n\t.reg .b128 d, c, n;\n\t"

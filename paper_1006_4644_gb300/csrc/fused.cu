@@ -21,6 +21,8 @@
 // sincos of an argument already in [-pi, pi) and one complex product.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include <type_traits>
 
 #include "internal.h"
@@ -440,9 +442,9 @@ __device__ __forceinline__ void p2_stage(E *v, E *row, int lt, const float2 *tw,
 // maximum.  Out of line and with scalar arguments, so that the common path
 // keeps every value in registers.
 __device__ __noinline__ void p2_emit(Slot *win, int64_t s, int64_t lo, int64_t window, float r2, float zr, float zi,
-                                     int *err)
+                                     int *err, int rounds)
 {
-    slot_max(win + (int)((s - lo) / window), make_key(r2, (uint32_t)s), atan2f(zi, zr), err);
+    slot_max(win + (int)((s - lo) / window), make_key(r2, (uint32_t)s), atan2f(zi, zr), err, rounds);
 }
 
 // Each lane's maximum of |z|^2 over this thread's outputs d = j + r L/RL of
@@ -487,6 +489,78 @@ __device__ __forceinline__ int64_t p2_find(const E *v, int lt, float M, const in
             }
         }
     return best;
+}
+
+// Epilogue of a row (pair) whose last stage left output d = lg + i L/PPT +
+// r L/RL in v[i RL + r].  Output d of lane l is sample s = c_l + n1 d with
+// c_l = c + l n1/2; |z|^2 is compared before the (positive) scaling.  The
+// maximum of |z|^2 over the NW warps that share `s_max` is reduced first
+// (`bar` is their barrier); only the threads that hold it then look for their
+// lowest sample with it and raise the peak slot of template t.
+template <int L, int RL, int PPT, int NW, typename E, typename Bar>
+__device__ __forceinline__ void p2_epilogue(const E *v, int lg, int c, int y, int t, const FusedArgs &p, float *s_max,
+                                            Bar bar)
+{
+    constexpr int NL = lanes_of<E>;
+    constexpr int TPR = L / PPT;
+    const float inv = p.invnorm[t];
+    const int n1 = p.n1;
+    const int64_t lo = p.lo, hi = p.hi;
+    int64_t cl[NL];
+    int dlo[NL], dhi[NL];
+    bool full = true;
+    float m[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        cl[l] = c + (int64_t)l * (n1 / 2);
+        dlo[l] = 0;
+        dhi[l] = L;
+        if (!(lo <= cl[l] && cl[l] + (int64_t)n1 * (L - 1) < hi)) {
+            full = false;
+            dlo[l] = (int)max((int64_t)0, (lo - cl[l] + n1 - 1) / n1);
+            dhi[l] = (int)min((int64_t)L, hi > cl[l] ? (hi - cl[l] + n1 - 1) / n1 : (int64_t)0);
+        }
+        m[l] = -1.f;
+    }
+    if (full) p2_max<L, RL, false, PPT>(v, lg, m, dlo, dhi);
+    else p2_max<L, RL, true, PPT>(v, lg, m, dlo, dhi);
+
+    float mx = m[0];
+#pragma unroll
+    for (int l = 1; l < NL; ++l) mx = fmaxf(mx, m[l]);
+    if (mx * inv > p.thr2) {
+        constexpr int TL = PPT / RL;
+        Slot *win = p.win + (size_t)y * p.nwin;
+#pragma unroll
+        for (int r = 0; r < RL; ++r)
+#pragma unroll
+            for (int i = 0; i < TL; ++i) {
+                const int d = lg + i * TPR + r * (L / RL);
+                const float2 a = abs2(v[i * RL + r]);
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    const float r2 = (l ? a.y : a.x) * inv;
+                    if (r2 > p.thr2 && d >= dlo[l] && d < dhi[l]) {
+                        const float2 z = lane(v[i * RL + r], l);
+                        p2_emit(win, cl[l] + (int64_t)n1 * d, lo, p.window, r2, z.x, z.y, p.err, p.cas_rounds);
+                    }
+                }
+            }
+    }
+    float wm = mx;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, off));
+    const int lane_id = threadIdx.x & 31, wid = (threadIdx.x >> 5) % NW;
+    if (lane_id == 0) s_max[wid] = wm;
+    bar();
+    float M = s_max[0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) M = fmaxf(M, s_max[w]);
+    if (M >= 0.f && mx == M) {
+        float2 zb = make_float2(0.f, 0.f);
+        const int64_t sb = p2_find<L, RL, PPT>(v, lg, M, cl, n1, dlo, dhi, zb);
+        slot_max(p.peak + t, make_key(M * inv, (uint32_t)sb), atan2f(zb.y, zb.x), p.err, p.cas_rounds);
+    }
 }
 
 // Grid (rows / RPC, B), rows = n1 (or n1 / 2 row pairs when PAIR).  RPC rows
@@ -581,68 +655,209 @@ __global__ void __launch_bounds__(RPC *L / PPT) k_pass2(const FusedArgs p)
     }
     p2_stage<L, RL, NSL, R2 == 1, PPT>(v, row, lg, tw1, wl);
 
-    // Epilogue.  Output d of lane l is sample s = c_l + n1 d with
-    // c_l = c + l n1/2; |z|^2 is compared before the (positive) scaling.  The
-    // CTA's maximum of |z|^2 is reduced first; only the threads that hold it
-    // then look for their lowest sample with it and raise the peak slot.
-    const float inv = p.invnorm[t];
-    const int n1 = p.n1;
-    const int64_t lo = p.lo, hi = p.hi;
-    int64_t cl[NL];
-    int dlo[NL], dhi[NL];
-    bool full = true;
-    float m[NL];
-#pragma unroll
-    for (int l = 0; l < NL; ++l) {
-        cl[l] = c + (int64_t)l * (n1 / 2);
-        dlo[l] = 0;
-        dhi[l] = L;
-        if (!(lo <= cl[l] && cl[l] + (int64_t)n1 * (L - 1) < hi)) {
-            full = false;
-            dlo[l] = (int)max((int64_t)0, (lo - cl[l] + n1 - 1) / n1);
-            dhi[l] = (int)min((int64_t)L, hi > cl[l] ? (hi - cl[l] + n1 - 1) / n1 : (int64_t)0);
-        }
-        m[l] = -1.f;
-    }
-    if (full) p2_max<L, RL, false, PPT>(v, lg, m, dlo, dhi);
-    else p2_max<L, RL, true, PPT>(v, lg, m, dlo, dhi);
+    p2_epilogue<L, RL, PPT, NW>(v, lg, c, y, t, p, s_max, [] { __syncthreads(); });
+}
 
-    float mx = m[0];
-#pragma unroll
-    for (int l = 1; l < NL; ++l) mx = fmaxf(mx, m[l]);
-    if (mx * inv > p.thr2) {
-        constexpr int TL = PPT / RL;
-        Slot *win = p.win + (size_t)y * p.nwin;
-#pragma unroll
-        for (int r = 0; r < RL; ++r)
-#pragma unroll
-            for (int i = 0; i < TL; ++i) {
-                const int d = lg + i * TPR + r * (L / RL);
-                const float2 a = abs2(v[i * RL + r]);
-#pragma unroll
-                for (int l = 0; l < NL; ++l) {
-                    const float r2 = (l ? a.y : a.x) * inv;
-                    if (r2 > p.thr2 && d >= dlo[l] && d < dhi[l]) {
-                        const float2 z = lane(v[i * RL + r], l);
-                        p2_emit(win, cl[l] + (int64_t)n1 * d, lo, p.window, r2, z.x, z.y, p.err);
-                    }
-                }
-            }
+// ------------------------------------------------------ streamed pass 2 ---
+// Pass 2 with its input streamed into shared memory by the bulk-copy (TMA)
+// engine, for paired rows of 4096 points (n2 = 4096: N = 2^18, 2^19, 2^20).
+// One persistent CTA per SM holds two teams of 256 threads, each with its own
+// padded exchange buffer, and one staging buffer S of a row pair.  The CTA's
+// row pairs i = blockIdx.x + k gridDim.x alternate between the teams (even k
+// team 0, odd k team 1).  A team waits for its row pair to land in S, reads
+// its stage-0 inputs from S, and as soon as all of its threads have read S
+// one of them issues the bulk copy of the CTA's next row pair (the other
+// team's) into S.  The copy then runs while both teams transform, so every SM
+// keeps a 64 KB load in flight without holding registers for it, which the
+// one-row-pair-per-CTA kernel could not do at two CTAs per SM.  Each team has
+// its own mbarrier, so a wait can never be satisfied by the other team's copy.
+//
+// Every wait is bounded on the global timer (p.copy_wait_ns, one second by
+// default).  A team whose wait gives up sets bit 4 of the error word
+// (CUI_ERR_TIMEOUT on the host), skips the rest of its work and stops issuing
+// copies, so the other team's wait gives up too; before the CTA exits, a copy
+// still in flight is waited for (always up to one second), so no copy lands in
+// a finished CTA's shared memory.
+constexpr int kStreamL = 4096;     // row length of the streamed pass 2
+constexpr int kStreamTeam = 256;   // threads per team: L / 16 points per thread
+constexpr int kStreamCopies = 4;   // bulk copies per row pair (one mbarrier transaction)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy completing `bytes` transactions on *bar
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait until the phase of *bar with parity `parity` has completed; false when
+// `limit_ns` pass first (at once for a limit of 0, which only tests use).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned long long limit_ns)
+{
+    if (limit_ns == 0) return false;
+    const uint32_t a = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        const unsigned long long now = global_ns();
+        if (it == 0) t0 = now;
+        else if (now - t0 > limit_ns) return false;
     }
-    float wm = mx;
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int nthreads)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <typename ST> __device__ __forceinline__ c2 pair_from(pair_t<ST> q);
+template <> __device__ __forceinline__ c2 pair_from<float2>(float4 q)
+{
+    return {make_float2(q.x, q.y), make_float2(q.z, q.w)};
+}
+template <> __device__ __forceinline__ c2 pair_from<__nv_bfloat162>(uint2 q)
+{
+    return {__bfloat1622float2(*(const __nv_bfloat162 *)&q.x), __bfloat1622float2(*(const __nv_bfloat162 *)&q.y)};
+}
+
+template <typename ST> constexpr size_t stream_stage_bytes() { return (size_t)kStreamL * sizeof(pair_t<ST>); }
+template <typename ST> constexpr size_t stream_smem()
+{
+    return stream_stage_bytes<ST>() + 2 * (size_t)padded<kStreamL>() * sizeof(c2);
+}
+
+// Issue the bulk copies of row pair `item` (ROWB bytes at ywork + item ROWB)
+// into S on *bar.  One thread.
+template <typename ST>
+__device__ __forceinline__ void stream_issue(const FusedArgs &p, int item, void *S, uint64_t *bar)
+{
+    constexpr unsigned ROWB = (unsigned)stream_stage_bytes<ST>();
+    constexpr unsigned PART = ROWB / kStreamCopies;
+    const char *src = (const char *)p.ywork + (size_t)item * ROWB;
+    // the team's generic-proxy reads of S are ordered before the copy's writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, ROWB);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, off));
-    const int lane_id = tid & 31, wid = tid >> 5;
-    if (lane_id == 0) s_max[wid] = wm;
+    for (int q = 0; q < kStreamCopies; ++q) bulk_load((char *)S + q * PART, src + q * PART, PART, bar);
+}
+
+// Grid min(SMs, rows pairs of the batch), 2 teams of 256 threads; row pair
+// i of the batch is template y = i / (n1/2), row pair c = i mod (n1/2).
+template <typename ST> __global__ void __launch_bounds__(2 * kStreamTeam, 1) k_pass2_stream(const FusedArgs p, int count)
+{
+    constexpr int L = kStreamL, PPT = 16, R = 16, TPR = kStreamTeam, NW = TPR / 32;
+    constexpr int LP = padded<L>();
+    constexpr size_t ROWB = stream_stage_bytes<ST>();
+    extern __shared__ __align__(128) float4 sm4[];
+    pair_t<ST> *S = reinterpret_cast<pair_t<ST> *>(sm4);
+    __shared__ float2 tw1[R * R];
+    __shared__ float s_max[2][NW];
+    __shared__ __align__(8) uint64_t full[2];
+    __shared__ int abort_flag[2], issued[2], consumed[2];
+    const int tid = threadIdx.x;
+    const int team = tid / TPR, lt = tid % TPR;
+    // last two stages on half-warp groups (as in k_pass2 for 4096-point rows)
+    const int lg = (lt & 15) * (L / 256) + (lt >> 4);
+    c2 *row = reinterpret_cast<c2 *>((char *)sm4 + ROWB) + team * LP;
+    const int npairs = p.n1 / 2;
+    const int total = count * npairs; // <= 4096 templates x 128 row pairs
+    const int G = gridDim.x;
+    const int bar_release = 1 + 2 * team, bar_team = 2 + 2 * team;
+
+    for (int m = tid; m < R * R; m += 2 * TPR) tw1[m] = turn((m % R) * (m / R), R * R);
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag[0] = abort_flag[1] = 0;
+        issued[0] = issued[1] = 0;
+        consumed[0] = consumed[1] = 0;
+    }
     __syncthreads();
-    float M = s_max[0];
-#pragma unroll
-    for (int w = 1; w < NW; ++w) M = fmaxf(M, s_max[w]);
-    if (M >= 0.f && mx == M) {
-        float2 zb = make_float2(0.f, 0.f);
-        const int64_t sb = p2_find<L, RL, PPT>(v, lg, M, cl, n1, dlo, dhi, zb);
-        slot_max(p.peak + t, make_key(M * inv, (uint32_t)sb), atan2f(zb.y, zb.x), p.err);
+    if (tid == 0 && (int)blockIdx.x < total) {
+        issued[0] = 1;
+        stream_issue<ST>(p, blockIdx.x, S, &full[0]);
     }
+    // root of the last stage's twiddles: the same for every row pair
+    const float2 wl = p2_root<R>(lg, L / R);
+
+    int j = 0; // row pairs this team has taken
+    for (int i = blockIdx.x + team * G; i < total; i += 2 * G, ++j) {
+        if (!mbar_wait(&full[team], j & 1, p.copy_wait_ns)) {
+            abort_flag[team] = 1;
+            atomicOr(p.err, 4);
+        }
+        c2 v[PPT];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = pair_from<ST>(S[lt + r * (L / R)]);
+        // S is free once every thread of the team has read it: the team's
+        // first warp waits for the others and issues the next row pair
+        if (lt < 32) {
+            named_sync(bar_release, TPR);
+            if (lt == 0 && !abort_flag[team] && i + G < total) {
+                issued[team ^ 1] += 1;
+                stream_issue<ST>(p, i + G, S, &full[team ^ 1]);
+            }
+        } else {
+            named_arrive(bar_release, TPR);
+        }
+        dft<R, +1>(v);
+        p2_store<L, R, 1, PPT>(v, row, lt);
+        named_sync(bar_team, TPR);
+        if (abort_flag[team]) break; // the same in every thread of the team after the barrier
+        const int y = i / npairs, c = i % npairs;
+        {
+            // Y is read exactly once: drop its L2 lines so that they are never written back
+            const char *yb = (const char *)p.ywork + (size_t)i * ROWB;
+            for (int m = lt; m < (int)(ROWB / 128); m += TPR)
+                asm volatile("discard.global.L2 [%0], 128;" ::"l"(yb + (size_t)m * 128) : "memory");
+        }
+        p2_stage<L, R, R, true, PPT>(v, row, lg, tw1);
+        __syncwarp();
+        p2_store<L, R, R, PPT>(v, row, lg);
+        __syncwarp();
+        p2_stage<L, R, L / R, false, PPT>(v, row, lg, tw1, &wl);
+        const int t = p.order[p.base + y];
+        p2_epilogue<L, R, PPT, NW>(v, lg, c, y, t, p, s_max[team], [bar_team] { named_sync(bar_team, TPR); });
+    }
+    if (lt == 0) consumed[team] = j;
+    __syncthreads();
+    // a team that gave up can leave one copy in flight: let it land first
+    if (tid == 0)
+        for (int q = 0; q < 2; ++q)
+            if (issued[q] > consumed[q] && !mbar_wait(&full[q], consumed[q] & 1, kCopyWaitNs)) atomicOr(p.err, 4);
 }
 
 // ------------------------------------------------------------ dispatch ----
@@ -662,6 +877,7 @@ static bool paired(int n2) { return n2 <= kPairMaxL; }
 size_t fused_pass1_smem(int n1, int ccols) { return (size_t)n1 * ccols * sizeof(float2); }
 size_t fused_pass2_smem(int n2, int rpc)
 {
+    if (rpc == 0) return stream_smem<float2>();
     int lp = n2 + n2 / 16; // padded<L>() of the kernel
     if (n2 == 4096) lp = padded<4096>();
     if (n2 == 16384) lp = padded<16384>();
@@ -676,8 +892,9 @@ bool fused_tiling_ok(int log2n, int n1, int ccols, int rpc)
     if (!fused_supported(log2n) || (n1 != 64 && n1 != 128 && n1 != 256) || (ccols != 16 && ccols != 32 && ccols != 64)) return false;
     const int64_t n2 = (int64_t(1) << log2n) / n1;
     if (n2 % ccols) return false;
-    static const int pass2[][2] = {{64, 32},  {128, 16}, {256, 8},  {512, 4},  {1024, 4},
-                                   {2048, 2}, {4096, 2}, {4096, 1}, {8192, 1}, {16384, 1}};
+    // rpc 0: the streamed persistent pass 2 (k_pass2_stream)
+    static const int pass2[][2] = {{64, 32},  {128, 16}, {256, 8},  {512, 4},  {1024, 4},         {2048, 2},
+                                   {4096, 2}, {4096, 1}, {4096, 0}, {8192, 1}, {16384, 1}};
     for (auto &q : pass2)
         if (q[0] == n2 && q[1] == rpc) return true;
     return false;
@@ -687,10 +904,11 @@ void fused_default_tiling(int log2n, int *n1, int *ccols, int *rpc)
 {
     static const int tab[23][2] = {{0, 0},  {0, 0},  {0, 0},  {0, 0},  {0, 0},  {0, 0},  {0, 0},  {0, 0},
                                    {0, 0},  {0, 0},  {0, 0},  {0, 0},  {64, 32}, {64, 16}, {64, 8}, {64, 4},
-                                   {64, 4}, {128, 4}, {256, 4}, {256, 2}, {256, 1}, {256, 1}, {256, 1}};
+                                   {64, 4}, {128, 4}, {256, 4}, {256, 2}, {256, 0}, {256, 1}, {256, 1}};
     *n1 = tab[log2n][0];
     *rpc = tab[log2n][1];
-    *ccols = 32;
+    // N = 2^20: the tiling the autotuner picks on GB300 (streamed pass 2, 16 columns per pass-1 CTA)
+    *ccols = log2n == 20 ? 16 : 32;
 }
 
 template <int N1, int R0, int R1, int C, typename ST>
@@ -736,9 +954,32 @@ static cudaError_t run_pass2(const FusedArgs &a, int count, cudaStream_t s)
     return cudaGetLastError();
 }
 
+static int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <typename ST> static cudaError_t run_pass2_stream(const FusedArgs &a, int count, cudaStream_t s)
+{
+    auto k = k_pass2_stream<ST>;
+    const size_t smem = stream_smem<ST>();
+    cudaError_t e = allow_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)count * (a.n1 / 2);
+    const int sms = sm_count();
+    if (sms <= 0) return cudaErrorInvalidDevice;
+    if (total <= 0) return cudaSuccess;
+    k<<<(unsigned)std::min<int64_t>(sms, total), 2 * kStreamTeam, smem, s>>>(a, count);
+    return cudaGetLastError();
+}
+
 template <typename ST> static cudaError_t pass2_dispatch(const FusedArgs &a, int count, cudaStream_t s)
 {
     const int L = a.n2, R = a.rpc;
+    if (L == kStreamL && R == 0) return run_pass2_stream<ST>(a, count, s);
     if (L == 64 && R == 32) return run_pass2<64, 32, ST, 4, 16, 1, 1>(a, count, s);
     if (L == 128 && R == 16) return run_pass2<128, 16, ST, 8, 16, 1, 1>(a, count, s);
     if (L == 256 && R == 8) return run_pass2<256, 8, ST, 16, 16, 1, 1>(a, count, s);
@@ -1088,7 +1329,7 @@ __global__ void k_finalize_windows(const FinalizeArgs a)
         decode(sl, tr.sample, tr.snr, tr.phase);
         const unsigned long long pos = atomicAdd(a.trig_count, 1ull);
         if (pos < (unsigned long long)a.trig_cap) a.trig[pos] = tr;
-        cluster_max(a.cluster + (i % a.nwin), sl.key, (uint32_t)tr.tmpl, sl.phase_bits, a.err);
+        cluster_max(a.cluster + (i % a.nwin), sl.key, (uint32_t)tr.tmpl, sl.phase_bits, a.err, a.cas_rounds);
         Slot zero = {0ull, 0u, 0u};
         a.win[i] = zero;
     }

@@ -89,6 +89,8 @@ struct FusedArgs {
     Slot *peak;             // [T] peak slots
     Slot *win;              // [B][nwin] window slots
     int *err;               // device error word
+    int cas_rounds;         // bound of the compare-and-swap loops (kCasRounds)
+    unsigned long long copy_wait_ns; // bound of a streamed pass-2 wait for its row pair
     int64_t n;
     int log2n, n1, n2, ccols, rpc;
     int k_low;
@@ -132,6 +134,7 @@ struct FinalizeArgs {
     unsigned long long *trig_count;
     Slot *cluster;           // [nwin] loudest trigger of each window over the bank
     int *err;
+    int cas_rounds;          // bound of the compare-and-swap loops
 };
 cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s);
 
@@ -148,6 +151,7 @@ struct PlainArgs {
     double *acc;             // sigma sum, one double
     Slot *peak, *win;
     int *err;
+    int cas_rounds; // bound of the compare-and-swap loops
     int64_t n;
     int log2n, pn_x2, k_low;
     double fs;

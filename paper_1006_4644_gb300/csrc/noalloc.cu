@@ -1,10 +1,9 @@
 // Allocation-free template normalisation (cui_template_sigma_noalloc).
 //
 // Some callers cannot allocate device memory at the moment they need a
-// result: code running while a CUDA stream is being captured into a graph
-// (where an allocation would break or be refused by the capture), pipelines
-// whose device memory is all owned by one pool allocator, or real-time loops
-// that must not take the time an allocation can take.  Such a caller may
+// result: pipelines whose device memory is all owned by one pool allocator
+// with a fixed budget, or real-time loops that must not take the time (and
+// the implicit synchronisation) a cudaMalloc can take.  Such a caller may
 // still need to renormalise a bank when its noise estimate changes.  This
 // entry point computes every template's sigma^2 for a given PSD with the same
 // kernels cui_segment_upload uses (amplitude table, prefix sums, per-template
@@ -44,6 +43,10 @@ NoallocScratch *g_noalloc_ptr[kMaxDevices] = {};
 } // namespace cui
 
 using namespace cui;
+
+// The lookup kernel scales by scales->scale_w, which must read exactly 1 here
+// (the array keeps the previous call's contents, so it is set on every call).
+__global__ void k_noalloc_unit_scales(SegScales *scales) { *scales = SegScales{0.0, 0.0, 1.0, 1.0}; }
 
 static cui_status noalloc_fail(cui_status st, const char *msg)
 {
@@ -99,8 +102,9 @@ extern "C" cui_status cui_template_sigma_noalloc(const double *psd_dev, int64_t 
 
     const cudaStream_t s = (cudaStream_t)stream;
     const double df = sample_rate / (double)n;
-    const int k_low = std::max(1, (int)std::ceil(f_low / df));
     const int64_t nh = n / 2;
+    // clamped before the conversion: an f_low at or above Nyquist leaves every band empty
+    const int k_low = std::max(1, (int)std::min<double>(std::ceil(f_low / df), (double)nh));
     // upper bins, copied from a stack buffer in chunks (a pageable source is
     // staged before cudaMemcpyAsync returns, so the buffer can be reused)
     int32_t chunk[512];
@@ -114,11 +118,8 @@ extern "C" cui_status cui_template_sigma_noalloc(const double *psd_dev, int64_t 
         e = cudaMemcpyAsync(sc->khi + t0, chunk, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return noalloc_fail(CUI_ERR_CUDA, cudaGetErrorString(e));
     }
-    // the array keeps the previous call's contents: the lookup reads
-    // scales.scale_w, which must be exactly 1 here
-    static const SegScales unit = {0.0, 0.0, 1.0, 1.0};
-    e = cudaMemcpyAsync(&sc->scales, &unit, sizeof unit, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return noalloc_fail(CUI_ERR_CUDA, cudaGetErrorString(e));
+    k_noalloc_unit_scales<<<1, 1, 0, s>>>(&sc->scales);
+    launched();
     launch_amp_table(sc->amp, nh, s);
     launch_prefix(psd_dev, sc->amp, n, k_low, sc->prefix, sc->bsum, s);
     launch_template_norm(sc->prefix, sc->khi, k_low, count, sample_rate, n, &sc->scales, sigma2_dev, sc->invnorm,

@@ -120,7 +120,7 @@ template <typename Rl> __global__ void k_plain_detect(const PlainArgs a, int t, 
         }
         if ((float)r2 > a.thr2) {
             const int m = (int)((j - a.lo) / a.window);
-            slot_max(a.win + m, key, (float)atan2((double)v.y, (double)v.x), a.err);
+            slot_max(a.win + m, key, (float)atan2((double)v.y, (double)v.x), a.err, a.cas_rounds);
         }
     }
     warp_max_key(best, bzr, bzi);
@@ -137,7 +137,7 @@ template <typename Rl> __global__ void k_plain_detect(const PlainArgs a, int t, 
         bzr = lane < nw ? s_zr[lane] : 0.f;
         bzi = lane < nw ? s_zi[lane] : 0.f;
         warp_max_key(best, bzr, bzi);
-        if (lane == 0 && best != 0ull) slot_max(a.peak + t, best, atan2f(bzi, bzr), a.err);
+        if (lane == 0 && best != 0ull) slot_max(a.peak + t, best, atan2f(bzi, bzr), a.err, a.cas_rounds);
     }
 }
 

@@ -131,6 +131,63 @@ def test_error_statuses(seg):
         _bank(m=(np.array([1.0, -1.0]), np.array([1.0, 1.0])))
 
 
+@pytest.mark.parametrize("case", ["fused_rounds0", "fused_rounds1_contended", "plain_rounds0", "streamed_wait0"])
+def test_bounded_waits_report_a_timeout_and_the_handle_recovers(case):
+    """The device waits are bounded and a wait that runs out is reported, not
+    hung on.  cui_bank_set_wait_bounds lowers the bounds: no round of the
+    compare-and-swap loops that raise the peak and window slots (every update
+    gives up), a single round under a zero threshold (thousands of samples
+    race for each window slot, so updates that lose a race give up), or a zero
+    time limit for the streamed pass 2's wait for its row pair (each team gives
+    up on its first row pair; the copy in flight still lands before the CTA
+    exits).  The next read-out returns CUI_ERR_TIMEOUT; with the defaults back,
+    a new upload and filter match the oracle again on the same handle."""
+    from paper_1006_4644_gb300 import CUI_PLAIN, CuiError, _lib
+
+    if case == "streamed_wait0":
+        w = synth.Workload("edge18", 1 << 18, 4096.0, 30.0, 7, 4, 1.0, 6.0, False, 1, 25.0, 25.0, 1.0, 4343)
+        strain, psd, dt, _ = make_segment(w)
+    else:
+        w = W
+        strain, psd, dt, _ = make_segment(W)
+    flags = CUI_PLAIN if case.startswith("plain") else 0
+    thr = 0.0 if "contended" in case else 6.0
+    with _bank(m=w.masses(), n=w.n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, flags=flags, snr_threshold=thr,
+               ) as b:
+        if case == "streamed_wait0":
+            b.set_tuning(64, 16, 0, w.n_templates)
+        b.upload(strain, psd)
+        if case == "streamed_wait0":
+            b.set_wait_bounds(-1, 0)
+        else:
+            b.set_wait_bounds(1 if "rounds1" in case else 0, -1)
+        b.filter()
+        with pytest.raises(CuiError) as e:
+            b.peaks()
+        assert e.value.status == _lib.CUI_ERR_TIMEOUT
+        b.set_wait_bounds()
+        b.upload(strain, psd)
+        b.filter()
+        peaks = b.peaks()
+        trig, _ = b.triggers(allow_overflow=True) if thr == 0.0 else b.triggers()
+    if thr > 0.0:
+        rep = compare_bank(w, dt, psd, peaks, trig, range(w.n_templates), 0, w.n, int(w.fs), thr)
+        assert rep.ok(), rep
+    else:
+        rep = compare_bank(w, dt, psd, peaks, trig[:0], range(w.n_templates), 0, w.n, int(w.fs), 1e9)
+        assert rep.ok(), rep
+
+
+def test_wait_bounds_above_the_defaults_are_rejected(seg):
+    from paper_1006_4644_gb300 import CuiError, _lib
+
+    with _bank() as b:
+        for args in ((1 << 21, -1), (-1, 2 * 10 ** 9)):
+            with pytest.raises(CuiError) as e:
+                b.set_wait_bounds(*args)
+            assert e.value.status == _lib.CUI_ERR_ARG
+
+
 def test_small_segments_use_the_plain_path():
     # N < 2^12 runs the per-template path; same answers as the oracle
     w = synth.Workload("tiny", 1 << 10, 4096.0, 100.0, 4, 4, 1.0, 3.0, False, 1, 15.0, 15.0, 1.0, 99)

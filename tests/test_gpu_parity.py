@@ -89,9 +89,17 @@ def seg256s():
     return make_segment(W2)
 
 
-def test_seg256s_bank1024_fused_full(seg256s):
+@pytest.mark.parametrize("tuning", [None, (256, 16, 0, 256)], ids=["default", "bench"])
+def test_seg256s_bank1024_fused_full(seg256s, tuning):
+    """The whole metric workload, in the default tiling and in the one the
+    benchmark's autotuner picks on GB300 (streamed pass 2, batches of 256)."""
     strain, psd, dt, (tmpl, j0, snr) = seg256s
-    peaks, trig, _ = _run(W2, strain, psd, 0)
+    with _bank(W2) as b:
+        b.upload(strain, psd)
+        if tuning:
+            b.set_tuning(*tuning)
+        b.filter()
+        peaks, trig = b.peaks(), b.triggers()[0]
     rep = compare_bank(W2, dt, psd, peaks, trig, range(W2.n_templates), 0, W2.n, int(W2.fs), 6.0)
     assert rep.ok(), rep
     assert rep.ambiguous <= 10, rep

@@ -23,7 +23,7 @@ def _tilings(bank, n):
     from paper_1006_4644_gb300 import CuiError
 
     out = []
-    for n1, cc, rpc in itertools.product([64, 128, 256], [16, 32, 64], [1, 2, 4, 8, 16, 32]):
+    for n1, cc, rpc in itertools.product([64, 128, 256], [16, 32, 64], [0, 1, 2, 4, 8, 16, 32]):
         try:
             bank.set_tuning(n1, cc, rpc, 3)
             out.append((n1, cc, rpc))
@@ -66,7 +66,7 @@ def test_full_template_groups_match_the_oracle(n1, cc):
     m1, m2 = w.masses()
     with Bank(m1, m2, n=n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, snr_threshold=5.0) as b:
         b.upload(strain, psd)
-        for rpc in (1, 2, 4, 8, 16, 32):
+        for rpc in (0, 1, 2, 4, 8, 16, 32):
             try:
                 b.set_tuning(n1, cc, rpc, w.n_templates)
                 break
@@ -99,3 +99,36 @@ def test_autotune_selects_a_valid_tiling():
         p = b.peaks()
     assert np.array_equal(p["sample"], ref["sample"])
     assert np.max(np.abs(p["snr"] - ref["snr"]) / ref["snr"]) < 1e-5
+
+
+@pytest.mark.parametrize("log2n,n1,count,batch", [(18, 64, 5, 5), (19, 128, 3, 2), (20, 256, 1, 1),
+                                                  (20, 256, 3, 3), (20, 256, 7, 4)])
+def test_streamed_pass2_equals_row_pair_kernel(log2n, n1, count, batch):
+    """The streamed persistent pass 2 (rpc 0: row pairs copied into shared
+    memory by the bulk-copy engine, two teams per CTA) runs the same arithmetic
+    in the same order as the one-row-pair-per-CTA kernel, so peaks and
+    triggers are bit-identical.  The cases cover fewer row pairs than SMs (one
+    template at 2^20: 128 row pairs, the second team idle), both teams, ragged
+    last batches, and a valid range that cuts rows; the error word must stay
+    clear (a bounded bulk-copy wait that gave up would read CUI_ERR_TIMEOUT)."""
+    from paper_1006_4644_gb300 import Bank
+
+    n = 1 << log2n
+    w = synth.Workload(f"stream{log2n}", n, 4096.0, 30.0, 7, count, 1.0, 8.0, False, 1, 15.0, 15.0, 1.0,
+                       611 + log2n + count)
+    strain, psd, dt, _ = make_segment(w)
+    m1, m2 = w.masses()
+    lo, hi = n // 7, n - n // 9
+    out = {}
+    for rpc in (1, 0):
+        with Bank(m1, m2, n=n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, snr_threshold=4.5, window=1000,
+                  valid=(lo, hi)) as b:
+            b.upload(strain, psd)
+            b.set_tuning(n1, 16, rpc, batch)
+            b.filter()
+            b.filter()  # a second call over the same buffers
+            out[rpc] = (b.peaks(), b.triggers()[0])
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    rep = compare_bank(w, dt, psd, out[0][0], out[0][1], range(w.n_templates), lo, hi, 1000, 4.5)
+    assert rep.ok(), rep

@@ -1,8 +1,8 @@
 """The allocation-free normalisation entry point (GPU).
 
-Some callers cannot allocate device memory when they need a result (work
-being captured into a CUDA graph, a pool-owned memory budget, a real-time
-loop); cui_template_sigma_noalloc serves them with scratch compiled into the
+Some callers cannot allocate device memory when they need a result (a
+pool-owned memory budget, a real-time loop that cannot wait for cudaMalloc);
+cui_template_sigma_noalloc serves them with scratch compiled into the
 library.  Its sigma^2 must equal what cui_bank_sigma gives for the same bank
 and PSD, on two calls in a row (the second call finds the previous call's
 contents in the shared scratch).  This file is collected last on purpose.
