@@ -99,6 +99,8 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self):
+        if getattr(self, "_summary", None) is not None:
+            return self._summary
         if not self.proc or not self.file:
             return None
         self.file.seek(0)
@@ -119,8 +121,9 @@ class Clocks:
         os.unlink(self.file.name)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        self._summary = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                         "samples": len(sm)}
+        return self._summary
 
 
 def build_segment(w, bank, psd):
@@ -177,15 +180,16 @@ def cpu_baseline(w, budget_s: float = 15.0, per_step: int | None = None, strain=
             "seconds": el, "results": res, "templates": sel}
 
 
-def accuracy(gpu_peaks, cpu):
+def accuracy(gpu_peaks, cpu, only=None):
     """The GPU peaks against the oracle's on the templates the CPU baseline
-    filtered (same strain and PSD): peak sample, SNR and phase."""
+    filtered (same strain and PSD), or on those of them in `only`: peak
+    sample, SNR and phase."""
     import numpy as np
 
     seen, rel, dphi, mism = set(), [], [], 0
     for t, r in zip(cpu["templates"], cpu["results"]):
         t = int(t)
-        if t in seen:
+        if t in seen or (only is not None and t not in only):
             continue
         seen.add(t)
         g = gpu_peaks[t]
@@ -534,20 +538,25 @@ def main():
     # secondary roof: the transform's 5 N log2 N flops per template (mostly adds
     # that cannot fuse) against one FP32 operation per lane per clock
     flop = 5.0 * w.n * math.log2(w.n) * n_units
-    alu_peak = 152 * 128 * 2.07e9 / 1e12
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    clk_sum = clk.summary()
+    mhz = clk_sum["sm_mhz"] if clk_sum else 2070.0  # the median SM clock sampled during the timed steps
+    alu_peak = sms * 128 * mhz * 1e6 / 1e12
     roof["alu_secondary"] = {"flop_per_template": 5.0 * w.n * math.log2(w.n),
                              "achieved_tflops": flop / ((p1[2] + p2[2]) / 1e3) / 1e12, "peak_tflops": alu_peak,
                              "frac": flop / ((p1[2] + p2[2]) / 1e3) / 1e12 / alu_peak,
-                             "peak_basis": "152 SMs x 128 FP32 lanes x 2.07 GHz, one add per lane per clock"}
+                             "peak_basis": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz "
+                                           f"({'median sampled' if clk_sum else 'maximum'} SM clock), "
+                                           "one add per lane per clock"}
 
     # end to end through the public API with pinned host buffers
     e2e = None
     if args.e2e:
         e2e = e2e_leg(w, m1, m2, strain, psd_fin, tuning, args, stream)
 
-    plain = None
+    plain, plain_peaks = None, None
     if args.plain_templates > 0:
-        plain = plain_leg(w, m1, m2, strain_d, psd_d, args, stream, value)
+        plain, plain_peaks = plain_leg(w, m1, m2, strain_d, psd_d, args, stream, value)
 
     cpu, acc = None, None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -556,6 +565,8 @@ def main():
         gpu_peaks = bank.peaks()
         cpu = cpu_baseline(w, strain=strain)
         acc = accuracy(gpu_peaks, cpu)
+        if plain is not None:  # the plain path at equal accuracy: its peaks against the same oracle results
+            plain["accuracy"] = accuracy(plain_peaks, cpu, only=set(range(plain["templates"])))
         for k in ("seconds", "results", "templates"):
             cpu.pop(k, None)
 
@@ -637,8 +648,9 @@ def plain_leg(w, m1, m2, strain_d, psd_d, args, stream, value):
     b.record(stream)
     torch.cuda.synchronize()
     pv = npl * reps / (a.elapsed_time(b) / 1e3)
+    peaks = pb.peaks()
     pb.close()
-    return {"value": pv, "unit": UNIT, "templates": npl, "mixed_over_plain": value / pv}
+    return {"value": pv, "unit": UNIT, "templates": npl, "mixed_over_plain": value / pv}, peaks
 
 
 if __name__ == "__main__":

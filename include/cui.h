@@ -233,6 +233,43 @@ cui_status cui_bank_set_band(cui_bank bank, double f_lo, double f_hi);
 cui_status cui_band_correlate(cui_bank bank, const int32_t *tmpl, const double *t_sec, int64_t n, double f_lo,
                               double f_hi, double *host_z, double *host_sigma2);
 
+/* The last step of the multi-band search: n candidates completed by the
+ * lower band and combined coherently.  Candidate i is template tmpl[i] of
+ * both banks (the same bank points, checked), detected by `high` (usually a
+ * short segment, band set to [f_split, ...)) at time t_high[i] seconds after
+ * high's first sample; `low` holds the data to complete it (the whole
+ * segment, or a decimated copy of its lower band) and the same instant is
+ * t_low[i] seconds after low's first sample.  With the band correlators of
+ * cui_band_correlate, z_h over [f_split, ...) on `high` and z_l over
+ * [..., f_split) on `low`:
+ *   rho_i = |z_h + z_l| / sqrt(sigma_h^2 + sigma_l^2),  phase_i = arg(z_h + z_l)
+ * written to host_rho and host_phase (n doubles each); host_sums (nullable)
+ * receives 6 n doubles (Re z_h, Im z_h, sigma_h^2, Re z_l, Im z_l,
+ * sigma_l^2).  The sums run on each bank's stream, the combination on low's
+ * after high's; synchronises both.  Paper: Sec. "Online analysis
+ * considerations" (the bands are analysed separately, the high one first,
+ * then the lower bands added for the candidates).  Errors: CUI_ERR_ARG (NULL
+ * pointers, different bank points, f_split not finite and > 0, a template
+ * out of range, a time not finite), CUI_ERR_STATE (plain bank, no segment),
+ * CUI_ERR_CUDA, CUI_ERR_TIMEOUT. */
+cui_status cui_band_combine(cui_bank high, const double *t_high, cui_bank low, const double *t_low,
+                            const int32_t *tmpl, int64_t n, double f_split, double *host_rho, double *host_phase,
+                            double *host_sums);
+
+/* The band of every template as the banks use it, on host arrays, without a
+ * GPU: *k_low_out (nullable) = max(1, ceil(f_low / df)) clamped to N/2,
+ * k_hi_out[t] = min(ceil(f_isco / df), N/2) with f_isco = 1 / (6^(3/2) pi M),
+ * M = (m1[t] + m2[t]) G Msun / c^3, df = sample_rate / n.  For callers that
+ * plan work by band (the sharding of a bank across GPUs weighs templates by
+ * k_hi - k_low), so that they use the library's own rule.  Paper: the
+ * low-frequency cut-off sets a template's length (Sec. "Online analysis
+ * considerations" and its footnote); the upper end at the innermost stable
+ * circular orbit is not in the paper (this library's reading).  Errors:
+ * CUI_ERR_ARG (NULL pointers, n not a power of two >= 2, non-finite or
+ * non-positive rate, f_low or masses). */
+cui_status cui_template_bands(const double *m1, const double *m2, int64_t n_templates, int64_t n,
+                              double sample_rate, double f_low, int32_t *k_low_out, int32_t *k_hi_out);
+
 /* The uploaded segment restricted to one band and resampled, for the
  * multi-band search: the series that the upper band is searched on (short
  * segments cut from it, at the full rate) and the decimated series that
@@ -408,6 +445,26 @@ cui_status cui_prescreen_gradient(cui_prescreen p, const float *feat_dev, const 
 cui_status cui_prescreen_get_state(cui_prescreen p, float *theta, float *m, float *v, int64_t *step);
 cui_status cui_prescreen_set_state(cui_prescreen p, const float *theta, const float *m, const float *v,
                                    int64_t step);
+/* Feature standardisation, part of the network's state: every forward pass
+ * (scores, training, gradients) reads x' = (x - mean_b) / std_b for the
+ * features x of band b.  A new handle has mean 0 and std 1.  fit_norm sets
+ * them from `count` feature rows on the device (FP64 sums of x and x^2 over
+ * the count * frames values of each band; std is the population standard
+ * deviation, 1 where it is zero or not finite), asynchronously; set_norm and
+ * get_norm take and return host arrays of `bands` floats and synchronise
+ * (set_norm: mean finite, std finite and > 0).  Not in the paper. */
+cui_status cui_prescreen_fit_norm(cui_prescreen p, const float *feat_dev, int64_t count);
+cui_status cui_prescreen_set_norm(cui_prescreen p, const float *mean, const float *stddev);
+cui_status cui_prescreen_get_norm(cui_prescreen p, float *mean, float *stddev);
+/* Ensemble scores: prob_dev[s][c] = (1/k) sum_e softmax(z_e(s))[c], the mean
+ * over the k networks nets[0 .. k) (same bands, frames and regions; each with
+ * its own standardisation) of their region probabilities for `count` feature
+ * rows, device arrays as for cui_prescreen_scores.  Runs on nets[0]'s stream
+ * in chunks of its max_batch, networks added in index order (deterministic);
+ * waits for the other networks' streams first when they differ.  Not in the
+ * paper. */
+cui_status cui_prescreen_ensemble_scores(const cui_prescreen *nets, int32_t k, const float *feat_dev, int64_t count,
+                                         float *prob_dev);
 /* Filtering order from region scores, on host arrays: the n_templates bank
  * points (m1[t], m2[t] in solar masses, finite and > 0) sorted by chirp mass
  * Mc = (m1 m2)^(3/5) / (m1 + m2)^(1/5) (equal Mc: lower index first) and cut

@@ -16,7 +16,12 @@ best solution", Sec. introduction footnote):
   (out[o, t] = b[o] + sum_{i,k} W[o, i, k] in[i, s t + k - 2]);
 * loss: soft-label cross entropy, mean over the batch;
 * gradients by hand-written reverse-mode differentiation, pinned in the tests
-  by central finite differences.
+  by central finite differences;
+* the optimiser step: Adam with bias correction (Kingma and Ba, "Adam: a
+  method for stochastic optimization", ICLR 2015, Algorithm 1);
+* feature standardisation: per-band mean and population standard deviation
+  over a set of feature rows, applied as (x - mean) / std before the network;
+* ensemble scores: the mean over networks of their softmax probabilities.
 
 Parameters travel as one flat vector in the order conv1.W, conv1.b, conv2.W,
 conv2.b, conv3.W, conv3.b, conv4.W, conv4.b, fc1.W, fc1.b, fc2.W, fc2.b
@@ -202,3 +207,37 @@ def regions_of_bank(m1, m2, regions: int = 100):
 
 def region_of(mc, bounds) -> int:
     return int(np.searchsorted(bounds, mc, side="left"))
+
+
+def adam_step(theta, m, v, g, step: int, lr: float, beta1: float, beta2: float, eps: float):
+    """One Adam update at step t = `step` (1 for the first), FP64:
+    m_t = b1 m + (1 - b1) g;  v_t = b2 v + (1 - b2) g^2;
+    m^ = m_t / (1 - b1^t);  v^ = v_t / (1 - b2^t);
+    theta_t = theta - lr m^ / (sqrt(v^) + eps).
+    Returns (theta_t, m_t, v_t)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    m_t = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v_t = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    m_hat = m_t / (1.0 - beta1 ** step)
+    v_hat = v_t / (1.0 - beta2 ** step)
+    return theta - lr * m_hat / (np.sqrt(v_hat) + eps), m_t, v_t
+
+
+def fit_norm(feats):
+    """Per-band mean and population standard deviation of feature rows
+    [count, B, T] over count * T values; a zero spread reads 1."""
+    f = np.asarray(feats, dtype=np.float64)
+    mean = f.mean(axis=(0, 2))
+    sd = np.sqrt(np.maximum(((f - mean[None, :, None]) ** 2).mean(axis=(0, 2)), 0.0))
+    return mean, np.where(sd > 0, sd, 1.0)
+
+
+def standardise(x, mean, sd):
+    """(x - mean_b) / sd_b for one feature row [B, T]."""
+    return (np.asarray(x, dtype=np.float64) - np.asarray(mean)[:, None]) / np.asarray(sd)[:, None]
+
+
+def ensemble_probabilities(logit_rows):
+    """Mean over networks of softmax(z): logit_rows [k][R] -> [R]."""
+    return np.mean([softmax(np.asarray(z, dtype=np.float64)) for z in logit_rows], axis=0)

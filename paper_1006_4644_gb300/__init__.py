@@ -22,7 +22,7 @@ from . import _lib
 from ._lib import (CUI_PLAIN, CUI_PLAIN_FP64, CUI_PSI_FP64, CUI_STORE_BF16, PEAK_DTYPE, TRIGGER_DTYPE, CuiError,
                    cui_bank_desc)
 
-__all__ = ["Bank", "Prescreen", "prescreen_rank", "CuiError", "CUI_PSI_FP64", "CUI_STORE_BF16", "CUI_PLAIN",
+__all__ = ["Bank", "Prescreen", "prescreen_rank", "ensemble_scores", "template_bands", "CuiError", "CUI_PSI_FP64", "CUI_STORE_BF16", "CUI_PLAIN",
            "CUI_PLAIN_FP64", "PEAK_DTYPE", "TRIGGER_DTYPE", "load"]
 
 load = _lib.load
@@ -176,6 +176,22 @@ class Bank:
                                               float(f_hi), z.ctypes.data, s2.ctypes.data), "cui_band_correlate")
         return z[0::2] + 1j * z[1::2], s2
 
+    def band_combine(self, t_high, low: "Bank", t_low, tmpl, f_split: float):
+        """Candidates detected by this bank (band [f_split, ...)) at t_high[i]
+        completed by `low` over [..., f_split) at t_low[i] and added coherently
+        (cui_band_combine): (rho, phase, sums [n, 6] = Re z_h, Im z_h,
+        sigma_h^2, Re z_l, Im z_l, sigma_l^2)."""
+        tm = np.ascontiguousarray(tmpl, dtype=np.int32)
+        th = np.ascontiguousarray(t_high, dtype=np.float64)
+        tl = np.ascontiguousarray(t_low, dtype=np.float64)
+        if not (tm.shape == th.shape == tl.shape):
+            raise ValueError("tmpl, t_high and t_low must have the same length")
+        rho, ph, sums = np.zeros(len(tm)), np.zeros(len(tm)), np.zeros((len(tm), 6))
+        _lib.check(self._l.cui_band_combine(self._h, th.ctypes.data, low._h, tl.ctypes.data, tm.ctypes.data, len(tm),
+                                            float(f_split), rho.ctypes.data, ph.ctypes.data, sums.ctypes.data),
+                   "cui_band_combine")
+        return rho, ph, sums
+
     def band_series(self, out_dev, f_lo: float = 0.0, f_hi: float = 0.0, decim: int = 1):
         """Write the uploaded segment restricted to [f_lo, f_hi) at the sample
         rate fs / decim into a float64 device tensor of N / decim samples."""
@@ -274,6 +290,33 @@ def prescreen_rank(m1, m2, scores, top_k: int | None = None):
     return out[: cnt.value].copy()
 
 
+def template_bands(m1, m2, *, n: int, fs: float, f_low: float):
+    """(k_low, k_hi per template) by the library's rule (cui_template_bands;
+    host only, no GPU)."""
+    lib = _lib.load()
+    a1 = np.ascontiguousarray(m1, dtype=np.float64)
+    a2 = np.ascontiguousarray(m2, dtype=np.float64)
+    if a1.shape != a2.shape:
+        raise ValueError("m1 and m2 must have the same length")
+    khi = np.zeros(len(a1), dtype=np.int32)
+    klo = C.c_int32()
+    _lib.check(lib.cui_template_bands(a1.ctypes.data, a2.ctypes.data, len(a1), int(n), float(fs), float(f_low),
+                                      C.byref(klo), khi.ctypes.data), "cui_template_bands")
+    return int(klo.value), khi
+
+
+def ensemble_scores(nets, feat_dev, out_dev):
+    """Mean over the networks of their region probabilities (softmax of the
+    scores) for feature rows [count, bands, frames] into out_dev [count,
+    regions] (cui_prescreen_ensemble_scores)."""
+    if not nets:
+        raise ValueError("no networks")
+    lib = nets[0]._l
+    arr = (C.c_void_p * len(nets))(*[p._h.value for p in nets])
+    _lib.check(lib.cui_prescreen_ensemble_scores(arr, len(nets), feat_dev.data_ptr(), feat_dev.shape[0],
+                                                 out_dev.data_ptr()), "cui_prescreen_ensemble_scores")
+
+
 class Prescreen:
     """The learned region prescreen (cui_prescreen_*): whitened band-power
     features, a conv1d + MLP scorer, and its training on the GPU.  Device
@@ -339,26 +382,47 @@ class Prescreen:
                                                    None if vv is None else vv.ctypes.data, int(step)),
                    "cui_prescreen_set_state")
 
+    def fit_norm(self, feat_dev):
+        """Set the per-band feature standardisation from these feature rows."""
+        _lib.check(self._l.cui_prescreen_fit_norm(self._h, feat_dev.data_ptr(), feat_dev.shape[0]),
+                   "cui_prescreen_fit_norm")
+
+    def get_norm(self):
+        mean, sd = np.zeros(self.bands, dtype=np.float32), np.zeros(self.bands, dtype=np.float32)
+        _lib.check(self._l.cui_prescreen_get_norm(self._h, mean.ctypes.data, sd.ctypes.data), "cui_prescreen_get_norm")
+        return mean, sd
+
+    def set_norm(self, mean, sd):
+        mean = np.ascontiguousarray(mean, dtype=np.float32)
+        sd = np.ascontiguousarray(sd, dtype=np.float32)
+        _lib.check(self._l.cui_prescreen_set_norm(self._h, mean.ctypes.data, sd.ctypes.data), "cui_prescreen_set_norm")
+
     def save(self, path: str):
-        """Checkpoint: JSON header line, then parameters, Adam moments (FP32)."""
+        """Checkpoint: JSON header line, then parameters, Adam moments and the
+        feature standardisation (mean, std per band), all FP32."""
         import json
 
         th, m, v, st = self.get_state()
+        mean, sd = self.get_norm()
         hdr = {"n_params": self.n_params, "step": st, "bands": self.bands, "frames": self.frames,
-               "regions": self.regions, "n": self.desc.n, "frame": self.desc.frame}
+               "regions": self.regions, "n": self.desc.n, "frame": self.desc.frame, "norm": True}
         with open(path, "wb") as fh:
             fh.write((json.dumps(hdr) + "\n").encode())
-            fh.write(th.tobytes() + m.tobytes() + v.tobytes())
+            fh.write(th.tobytes() + m.tobytes() + v.tobytes() + mean.tobytes() + sd.tobytes())
 
     def load(self, path: str):
         import json
 
         with open(path, "rb") as fh:
             hdr = json.loads(fh.readline())
-            if hdr["n_params"] != self.n_params:
+            if hdr["n_params"] != self.n_params or hdr["bands"] != self.bands:
                 raise ValueError("checkpoint does not match this network")
-            a = np.frombuffer(fh.read(), dtype=np.float32).reshape(3, self.n_params)
+            raw = np.frombuffer(fh.read(), dtype=np.float32)
+        a = raw[:3 * self.n_params].reshape(3, self.n_params)
         self.set_state(a[0], a[1], a[2], hdr["step"])
+        if hdr.get("norm"):
+            rest = raw[3 * self.n_params:]
+            self.set_norm(rest[:self.bands], rest[self.bands:2 * self.bands])
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -72,6 +72,8 @@ def load():
     lib.cui_td_template.argtypes = [vp, C.c_int64, C.c_int32, vp, vp]
     lib.cui_bank_set_band.argtypes = [vp, C.c_double, C.c_double]
     lib.cui_band_correlate.argtypes = [vp, vp, vp, C.c_int64, C.c_double, C.c_double, vp, vp]
+    lib.cui_band_combine.argtypes = [vp, vp, vp, vp, vp, C.c_int64, C.c_double, vp, vp, vp]
+    lib.cui_template_bands.argtypes = [vp, vp, C.c_int64, C.c_int64, C.c_double, C.c_double, vp, vp]
     lib.cui_segment_band_series.argtypes = [vp, C.c_double, C.c_double, C.c_int32, vp]
     lib.cui_bank_sigma.argtypes = [vp, vp]
     lib.cui_bank_template.argtypes = [vp, C.c_int64, vp]
@@ -90,7 +92,8 @@ def load():
                  "cui_cluster_triggers", "cui_trigger_chisq", "cui_td_template", "cui_bank_set_band",
                  "cui_band_correlate", "cui_segment_band_series", "cui_results",
                  "cui_bank_sigma", "cui_bank_template", "cui_trace_enable", "cui_trace_read",
-                 "cui_bank_get_tuning", "cui_bank_set_tuning", "cui_bank_autotune", "cui_bank_set_wait_bounds"):
+                 "cui_bank_get_tuning", "cui_bank_set_tuning", "cui_bank_autotune", "cui_bank_set_wait_bounds",
+                 "cui_band_combine", "cui_template_bands"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -130,8 +133,14 @@ def load_prescreen(lib):
     lib.cui_prescreen_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_int64)]
     lib.cui_prescreen_set_state.argtypes = [vp, vp, vp, vp, C.c_int64]
     lib.cui_prescreen_rank.argtypes = [vp, vp, C.c_int64, vp, C.c_int32, C.c_int32, vp, C.POINTER(C.c_int64)]
+    lib.cui_prescreen_fit_norm.argtypes = [vp, vp, C.c_int64]
+    lib.cui_prescreen_set_norm.argtypes = [vp, vp, vp]
+    lib.cui_prescreen_get_norm.argtypes = [vp, vp, vp]
+    lib.cui_prescreen_ensemble_scores.argtypes = [vp, C.c_int32, vp, C.c_int64, vp]
     for name in ("cui_prescreen_create", "cui_prescreen_info", "cui_prescreen_features", "cui_prescreen_bank_features",
                  "cui_prescreen_scores", "cui_prescreen_train_step", "cui_prescreen_gradient",
-                 "cui_prescreen_get_state", "cui_prescreen_set_state", "cui_prescreen_rank"):
+                 "cui_prescreen_get_state", "cui_prescreen_set_state", "cui_prescreen_rank",
+                 "cui_prescreen_fit_norm", "cui_prescreen_set_norm", "cui_prescreen_get_norm",
+                 "cui_prescreen_ensemble_scores"):
         getattr(lib, name).restype = C.c_int
     return lib

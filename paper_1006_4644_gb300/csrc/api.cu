@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "bands.h"
 #include "internal.h"
 #include "td.h"
 
@@ -432,7 +433,7 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     b->nt = n_templates;
     b->df = d.sample_rate / (double)d.n;
     // clamped before the conversion: an f_low at or above Nyquist leaves every band empty
-    b->k_low = std::max<int>(1, (int)std::min<double>(std::ceil(d.f_low / b->df), (double)b->nh));
+    b->k_low = band_k_low(d.f_low, b->df, b->nh);
     b->band_lo = b->k_low;
     b->band_hi = (int)(d.n / 2);
     b->fused = !(d.flags & CUI_PLAIN) && fused_supported(b->log2n);
@@ -449,9 +450,7 @@ extern "C" cui_status cui_bank_create(const cui_bank_desc *desc, const double *m
     b->h_khi.resize(nt);
     for (int64_t t = 0; t < nt; ++t) {
         const double M = (m1[t] + m2[t]) * kMsunS;
-        const double f_isco = 1.0 / (std::pow(6.0, 1.5) * kPi * M);
-        const double kh = std::ceil(f_isco / b->df);
-        b->h_khi[t] = (int32_t)std::min<double>(kh, (double)b->nh);
+        b->h_khi[t] = band_k_hi(m1[t], m2[t], b->df, b->nh);
         phase_coefficients(m1[t], m2[t], pn, b->df, &coef[t * kNB]);
         for (int i = 0; i < kNB; ++i) {
             const double c = coef[t * kNB + i];
@@ -1182,57 +1181,146 @@ extern "C" cui_status cui_segment_band_series(cui_bank b, double f_lo, double f_
     return CUI_OK;
 }
 
+// Validated band-sum queries of one bank: template ids, times as 64-bit
+// fractions of the segment, the band's bins and the physical-unit factors.
+struct BandQuery {
+    std::vector<int32_t> t;
+    std::vector<uint64_t> u;
+    int ka = 0, kb = 0;
+    double zfac = 0, sfac = 0;
+};
+
+static cui_status band_query(cui_bank b, const int32_t *tmpl, const double *t_sec, int64_t n, double f_lo,
+                             double f_hi, BandQuery &q)
+{
+    if (!std::isfinite(f_lo) || !std::isfinite(f_hi)) return fail(CUI_ERR_ARG, "band edges must be finite");
+    if (!b->fused) return fail(CUI_ERR_STATE, "band sums need the fused path (N >= 2^12, no CUI_PLAIN)");
+    if (!b->have_segment) return fail(CUI_ERR_STATE, "no segment uploaded");
+    const double T = (double)b->n / b->desc.sample_rate;
+    q.t.resize(n);
+    q.u.resize(n);
+    for (int64_t i = 0; i < n; ++i) {
+        if (tmpl[i] < 0 || tmpl[i] >= b->nt) return fail(CUI_ERR_ARG, "query %lld: template out of range", (long long)i);
+        if (!std::isfinite(t_sec[i])) return fail(CUI_ERR_ARG, "query %lld: time must be finite", (long long)i);
+        q.t[i] = tmpl[i];
+        // t / T mod 1 as a 64-bit fraction (exact for sample times j / fs)
+        double fr = t_sec[i] / T;
+        fr -= std::floor(fr);
+        const double x = std::ldexp(fr, 64);
+        q.u[i] = x >= 18446744073709551616.0 ? 0ull : (uint64_t)x;
+    }
+    const double klo = std::ceil(f_lo / b->df), khi = std::ceil(f_hi / b->df);
+    q.ka = (int)std::max<double>(b->k_low, std::min<double>(klo, (double)b->nh));
+    q.kb = f_hi <= 0.0 ? (int)b->nh : (int)std::max<double>(q.ka, std::min<double>(khi, (double)b->nh));
+    const double df = b->df;
+    q.zfac = 4.0 * df * std::pow(df, -7.0 / 6.0);
+    q.sfac = 4.0 * df * std::pow(df, -7.0 / 3.0);
+    return CUI_OK;
+}
+
+// Device buffers of one batch of band sums, freed by the destructor (after the
+// caller's synchronisation).
+struct BandBufs {
+    int32_t *t = nullptr;
+    uint64_t *u = nullptr;
+    double *out = nullptr;
+    ~BandBufs()
+    {
+        cudaFree(t);
+        cudaFree(u);
+        cudaFree(out);
+    }
+};
+
+// Queue the sums of q on the bank's stream into bufs.out[3 i ..] = (Re z, Im z, sigma^2).
+static cudaError_t band_queue(cui_bank b, const BandQuery &q, BandBufs &bufs)
+{
+    const int64_t n = (int64_t)q.t.size();
+    const cudaStream_t s = b->stream;
+    cudaError_t e = cudaMalloc(&bufs.t, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&bufs.u, sizeof(uint64_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&bufs.out, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bufs.t, q.t.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bufs.u, q.u.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_band(fused_args(b, b->d_iota, 0), b->d_prefix, b->d_khi0, bufs.t, bufs.u, (int)n, q.ka, q.kb,
+                        b->d_scales, q.zfac, q.sfac, bufs.out, s);
+    return e;
+}
+
 extern "C" cui_status cui_band_correlate(cui_bank b, const int32_t *tmpl, const double *t_sec, int64_t n,
                                          double f_lo, double f_hi, double *host_z, double *host_sigma2)
 {
     if (!b) return fail(CUI_ERR_ARG, "bank is NULL");
     if (n < 0 || n > (int64_t(1) << 30) || (n > 0 && (!tmpl || !t_sec || !host_z)))
         return fail(CUI_ERR_ARG, "bad query count or NULL pointers");
-    if (!std::isfinite(f_lo) || !std::isfinite(f_hi)) return fail(CUI_ERR_ARG, "band edges must be finite");
-    if (!b->fused) return fail(CUI_ERR_STATE, "band sums need the fused path (N >= 2^12, no CUI_PLAIN)");
-    if (!b->have_segment) return fail(CUI_ERR_STATE, "no segment uploaded");
-    if (n == 0) return CUI_OK;
-    const double T = (double)b->n / b->desc.sample_rate;
-    std::vector<int32_t> ht(n);
-    std::vector<uint64_t> hu(n);
-    for (int64_t i = 0; i < n; ++i) {
-        if (tmpl[i] < 0 || tmpl[i] >= b->nt) return fail(CUI_ERR_ARG, "query %lld: template out of range", (long long)i);
-        if (!std::isfinite(t_sec[i])) return fail(CUI_ERR_ARG, "query %lld: time must be finite", (long long)i);
-        ht[i] = tmpl[i];
-        // t / T mod 1 as a 64-bit fraction (exact for sample times j / fs)
-        double fr = t_sec[i] / T;
-        fr -= std::floor(fr);
-        const double x = std::ldexp(fr, 64);
-        hu[i] = x >= 18446744073709551616.0 ? 0ull : (uint64_t)x;
-    }
-    const double klo = std::ceil(f_lo / b->df), khi = std::ceil(f_hi / b->df);
-    const int ka = (int)std::max<double>(b->k_low, std::min<double>(klo, (double)b->nh));
-    const int kb = f_hi <= 0.0 ? (int)b->nh : (int)std::max<double>(ka, std::min<double>(khi, (double)b->nh));
-    const double df = b->df;
-    const double zfac = 4.0 * df * std::pow(df, -7.0 / 6.0), sfac = 4.0 * df * std::pow(df, -7.0 / 3.0);
-    const cudaStream_t s = b->stream;
-    int32_t *d_t = nullptr;
-    uint64_t *d_u = nullptr;
-    double *d_out = nullptr;
+    BandQuery q;
+    cui_status st = band_query(b, tmpl, t_sec, n, f_lo, f_hi, q);
+    if (st != CUI_OK || n == 0) return st;
     std::vector<double> out(3 * n);
-    cudaError_t e = cudaMalloc(&d_t, sizeof(int32_t) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&d_u, sizeof(uint64_t) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(double) * 3 * n);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_t, ht.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_u, hu.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s);
+    BandBufs bufs;
+    cudaError_t e = band_queue(b, q, bufs);
     if (e == cudaSuccess)
-        e = launch_band(fused_args(b, b->d_iota, 0), b->d_prefix, b->d_khi0, d_t, d_u, (int)n, ka, kb, b->d_scales,
-                        zfac, sfac, d_out, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), d_out, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);
-    cui_status st = e == cudaSuccess ? sync_and_check(b) : cuda_fail(e, "band sums");
-    cudaFree(d_t);
-    cudaFree(d_u);
-    cudaFree(d_out);
+        e = cudaMemcpyAsync(out.data(), bufs.out, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, b->stream);
+    st = e == cudaSuccess ? sync_and_check(b) : cuda_fail(e, "band sums");
     if (st != CUI_OK) return st;
     for (int64_t i = 0; i < n; ++i) {
         host_z[2 * i] = out[3 * i];
         host_z[2 * i + 1] = out[3 * i + 1];
         if (host_sigma2) host_sigma2[i] = out[3 * i + 2];
+    }
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_band_combine(cui_bank high, const double *t_high, cui_bank low, const double *t_low,
+                                       const int32_t *tmpl, int64_t n, double f_split, double *host_rho,
+                                       double *host_phase, double *host_sums)
+{
+    if (!high || !low) return fail(CUI_ERR_ARG, "both banks must be non-NULL");
+    if (n < 0 || n > (int64_t(1) << 30) || (n > 0 && (!tmpl || !t_high || !t_low || !host_rho || !host_phase)))
+        return fail(CUI_ERR_ARG, "bad candidate count or NULL pointers");
+    if (high->nt != low->nt) return fail(CUI_ERR_ARG, "the two banks hold different numbers of templates");
+    for (int64_t t = 0; t < high->nt; ++t)
+        if (high->h_mass[2 * t] != low->h_mass[2 * t] || high->h_mass[2 * t + 1] != low->h_mass[2 * t + 1])
+            return fail(CUI_ERR_ARG, "template %lld differs between the two banks", (long long)t);
+    if (!std::isfinite(f_split) || !(f_split > 0)) return fail(CUI_ERR_ARG, "f_split must be finite and > 0");
+    BandQuery qh, ql;
+    cui_status st = band_query(high, tmpl, t_high, n, f_split, 0.0, qh);
+    if (st == CUI_OK) st = band_query(low, tmpl, t_low, n, 0.0, f_split, ql);
+    if (st != CUI_OK || n == 0) return st;
+    BandBufs bh, bl;
+    double *d_res = nullptr;
+    std::vector<double> res(2 * n), sums(host_sums ? 6 * n : 0);
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = band_queue(high, qh, bh);
+    if (e == cudaSuccess) e = band_queue(low, ql, bl);
+    if (e == cudaSuccess) e = cudaMalloc(&d_res, sizeof(double) * 2 * n);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, high->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(low->stream, ev, 0);
+    if (e == cudaSuccess) e = launch_band_combine(bh.out, bl.out, (int)n, d_res, low->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(res.data(), d_res, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, low->stream);
+    if (e == cudaSuccess && host_sums) {
+        e = cudaMemcpyAsync(sums.data(), bh.out, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, low->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sums.data() + 3 * n, bl.out, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost,
+                                low->stream);
+    }
+    st = e == cudaSuccess ? sync_and_check(high) : cuda_fail(e, "band combination");
+    if (st == CUI_OK) st = sync_and_check(low);
+    if (ev) cudaEventDestroy(ev);
+    cudaFree(d_res);
+    if (st != CUI_OK) return st;
+    for (int64_t i = 0; i < n; ++i) {
+        host_rho[i] = res[2 * i];
+        host_phase[i] = res[2 * i + 1];
+        if (host_sums) {
+            for (int c = 0; c < 3; ++c) {
+                host_sums[6 * i + c] = sums[3 * i + c];
+                host_sums[6 * i + 3 + c] = sums[3 * n + 3 * i + c];
+            }
+        }
     }
     return CUI_OK;
 }

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <mutex>
 
+#include "bands.h"
 #include "internal.h"
 
 namespace cui {
@@ -103,18 +104,13 @@ extern "C" cui_status cui_template_sigma_noalloc(const double *psd_dev, int64_t 
     const cudaStream_t s = (cudaStream_t)stream;
     const double df = sample_rate / (double)n;
     const int64_t nh = n / 2;
-    // clamped before the conversion: an f_low at or above Nyquist leaves every band empty
-    const int k_low = std::max(1, (int)std::min<double>(std::ceil(f_low / df), (double)nh));
+    const int k_low = band_k_low(f_low, df, nh); // clamped: f_low at or above Nyquist leaves every band empty
     // upper bins, copied from a stack buffer in chunks (a pageable source is
     // staged before cudaMemcpyAsync returns, so the buffer can be reused)
     int32_t chunk[512];
     for (int64_t t0 = 0; t0 < count; t0 += 512) {
         const int64_t m = std::min<int64_t>(512, count - t0);
-        for (int64_t i = 0; i < m; ++i) {
-            const double M = (m1[t0 + i] + m2[t0 + i]) * 4.925490947e-6;
-            const double f_isco = 1.0 / (std::pow(6.0, 1.5) * kPi * M);
-            chunk[i] = (int32_t)std::min<double>(std::ceil(f_isco / df), (double)nh);
-        }
+        for (int64_t i = 0; i < m; ++i) chunk[i] = band_k_hi(m1[t0 + i], m2[t0 + i], df, nh);
         e = cudaMemcpyAsync(sc->khi + t0, chunk, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return noalloc_fail(CUI_ERR_CUDA, cudaGetErrorString(e));
     }

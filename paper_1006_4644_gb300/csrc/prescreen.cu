@@ -100,6 +100,7 @@ __global__ void k_ps_frames(const float2 *__restrict__ x, const int2 *__restrict
 // ------------------------------------------------------------- network ----
 struct PsArgs {
     const __nv_bfloat16 *w; // BF16 parameters
+    const float *norm;      // [2 B]: per-band mean, then 1 / standard deviation
     PsLayout L;
 };
 
@@ -194,7 +195,9 @@ __global__ void __launch_bounds__(PS_NT) k_ps_net(const PsArgs a, const float *_
     float *red = dB + PS_CH * T;       // [32] reduction scratch
     const int NT = blockDim.x;
 
-    for (int i = threadIdx.x; i < B * T; i += NT) act[0][i] = feat[(int64_t)s * B * T + i];
+    // standardised features (x - mean_b) / std_b
+    for (int i = threadIdx.x; i < B * T; i += NT)
+        act[0][i] = (feat[(int64_t)s * B * T + i] - a.norm[i / T]) * a.norm[B + i / T];
     // ---- forward
     for (int l = 0; l < 4; ++l) {
         const int cin = l == 0 ? B : PS_CH;
@@ -334,6 +337,67 @@ size_t ps_net_smem(const PsLayout &L)
     return f * sizeof(float);
 }
 
+// Per-band standardisation of `count` feature rows [count][B][T]: one CTA per
+// band sums x and x^2 in FP64 over the count * T values, each thread a fixed
+// strided share and the block a fixed-order reduction (deterministic).
+// norm[b] = mean, norm[B + b] = 1 / std (population), 1 where the spread is
+// zero or not finite.
+__global__ void k_ps_fit_norm(const float *__restrict__ feat, int64_t count, int B, int T, float *__restrict__ norm)
+{
+    __shared__ double s1[256], s2[256];
+    const int b = blockIdx.x;
+    double a1 = 0.0, a2 = 0.0;
+    const int64_t tot = count * T;
+    for (int64_t i = threadIdx.x; i < tot; i += blockDim.x) {
+        const double x = feat[(i / T) * B * T + (int64_t)b * T + i % T];
+        a1 += x;
+        a2 += x * x;
+    }
+    s1[threadIdx.x] = a1;
+    s2[threadIdx.x] = a2;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            s1[threadIdx.x] += s1[threadIdx.x + h];
+            s2[threadIdx.x] += s2[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mean = s1[0] / (double)tot;
+        const double var = s2[0] / (double)tot - mean * mean;
+        const double sd = var > 0.0 ? sqrt(var) : 0.0;
+        norm[b] = (float)mean;
+        norm[B + b] = sd > 0.0 && isfinite(sd) ? (float)(1.0 / sd) : 1.f;
+    }
+}
+
+// probs[s][c] (+)= softmax(logits[s])[c] / k for `count` rows of R logits;
+// one warp per row.  `first` overwrites, else accumulates (networks are added
+// in a fixed order, so the mean is deterministic).
+__global__ void k_ps_softmax_mean(const float *__restrict__ logits, int count, int R, float inv_k, int first,
+                                  float *__restrict__ probs)
+{
+    const int lane = threadIdx.x & 31;
+    for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < count; s += (gridDim.x * blockDim.x) >> 5) {
+        const float *z = logits + (int64_t)s * R;
+        float mx = -INFINITY;
+        for (int c = lane; c < R; c += 32) mx = fmaxf(mx, z[c]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        float se = 0.f;
+        for (int c = lane; c < R; c += 32) se += expf(z[c] - mx);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+        const float sc = inv_k / se;
+        float *out = probs + (int64_t)s * R;
+        for (int c = lane; c < R; c += 32) {
+            const float q = expf(z[c] - mx) * sc;
+            out[c] = first ? q : out[c] + q;
+        }
+    }
+}
+
 // g[p] = (1/count) sum_s grads[s][p], summed in sample order (deterministic)
 __global__ void k_ps_reduce(const float *__restrict__ grads, int64_t P, int count, float *__restrict__ g)
 {
@@ -413,6 +477,8 @@ struct cui_prescreen_s {
     float *d_theta = nullptr, *d_m = nullptr, *d_v = nullptr, *d_g = nullptr, *d_grads = nullptr;
     __nv_bfloat16 *d_w = nullptr;
     float *d_loss = nullptr;
+    float *d_norm = nullptr;   // [2 B] feature standardisation (mean, 1 / std)
+    float *d_logits = nullptr; // [max_batch][regions] scratch of the ensemble scores
     int64_t step = 0;
 };
 
@@ -432,7 +498,7 @@ static cui_status ps_fail(cui_status st, const char *msg)
 static void ps_release(cui_prescreen p)
 {
     void *ptrs[] = {p->d_band, p->tw.lo64, p->tw.hi64, p->tw.lo32, p->tw.hi32, p->d_fa, p->d_fb, p->d_theta,
-                    p->d_m, p->d_v, p->d_g, p->d_grads, p->d_w, p->d_loss};
+                    p->d_m, p->d_v, p->d_g, p->d_grads, p->d_w, p->d_loss, p->d_norm, p->d_logits};
     for (void *q : ptrs)
         if (q) cudaFree(q);
 }
@@ -486,6 +552,8 @@ extern "C" cui_status cui_prescreen_create(const cui_prescreen_desc *d, cui_pres
     chk(cudaMalloc(&p->d_grads, sizeof(float) * P * d->max_batch));
     chk(cudaMalloc(&p->d_w, sizeof(__nv_bfloat16) * P));
     chk(cudaMalloc(&p->d_loss, sizeof(float) * d->max_batch));
+    chk(cudaMalloc(&p->d_norm, sizeof(float) * 2 * d->bands));
+    chk(cudaMalloc(&p->d_logits, sizeof(float) * d->max_batch * d->regions));
     if (e != cudaSuccess) {
         ps_release(p);
         delete p;
@@ -499,6 +567,13 @@ extern "C" cui_status cui_prescreen_create(const cui_prescreen_desc *d, cui_pres
     launched(2);
     chk(cudaMemsetAsync(p->d_m, 0, sizeof(float) * P, s));
     chk(cudaMemsetAsync(p->d_v, 0, sizeof(float) * P, s));
+    {
+        // no standardisation until one is fitted or set: mean 0, 1 / std = 1
+        std::vector<float> unit(2 * d->bands, 0.f);
+        std::fill(unit.begin() + d->bands, unit.end(), 1.f);
+        chk(cudaMemcpyAsync(p->d_norm, unit.data(), sizeof(float) * unit.size(), cudaMemcpyHostToDevice, s));
+        chk(cudaStreamSynchronize(s)); // the host vector is pageable and goes out of scope
+    }
     chk(cudaFuncSetAttribute(k_ps_net, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps_net_smem(p->L)));
     chk(cudaGetLastError());
     chk(cudaStreamSynchronize(s));
@@ -579,7 +654,7 @@ extern "C" cui_status cui_prescreen_scores(cui_prescreen p, const float *feat_de
 {
     if (!scores_dev) return ps_fail(CUI_ERR_ARG, "scores_dev is NULL");
     if (!p || !feat_dev || count < 0) return ps_fail(CUI_ERR_ARG, "bad arguments");
-    PsArgs a = {p->d_w, p->L};
+    PsArgs a = {p->d_w, p->d_norm, p->L};
     // the attribute is per kernel, shared by prescreens of other sizes: set it per call
     PS_TRY(cudaFuncSetAttribute(k_ps_net, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps_net_smem(p->L)));
     for (int64_t s0 = 0; s0 < count; s0 += 65535) {
@@ -594,7 +669,7 @@ extern "C" cui_status cui_prescreen_scores(cui_prescreen p, const float *feat_de
 
 static cui_status ps_grad(cui_prescreen p, const float *feat, const float *target, int64_t count)
 {
-    PsArgs a = {p->d_w, p->L};
+    PsArgs a = {p->d_w, p->d_norm, p->L};
     PS_TRY(cudaFuncSetAttribute(k_ps_net, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps_net_smem(p->L)));
     k_ps_net<<<(unsigned)count, PS_NT, ps_net_smem(p->L), p->stream>>>(a, feat, target, nullptr, p->d_loss,
                                                                        p->d_grads);
@@ -637,7 +712,9 @@ extern "C" cui_status cui_prescreen_train_step(cui_prescreen p, const float *fea
     if ((st = ps_grad(p, feat_dev, target_dev, count)) != CUI_OK) return st;
     p->step += 1;
     const cui_prescreen_desc &d = p->desc;
-    const float c1 = 1.f - std::pow(d.beta1, (float)p->step), c2 = 1.f - std::pow(d.beta2, (float)p->step);
+    // bias corrections 1 - beta^t in FP64 (in FP32, 1 - 0.999^t loses four digits to cancellation)
+    const float c1 = (float)(1.0 - std::pow((double)d.beta1, (double)p->step));
+    const float c2 = (float)(1.0 - std::pow((double)d.beta2, (double)p->step));
     k_ps_adam<<<(unsigned)((p->L.total + 255) / 256), 256, 0, p->stream>>>(p->d_theta, p->d_m, p->d_v, p->d_g,
                                                                           p->d_w, p->L.total, d.lr, d.beta1,
                                                                           d.beta2, d.eps, c1, c2);
@@ -674,6 +751,77 @@ extern "C" cui_status cui_prescreen_set_state(cui_prescreen p, const float *thet
     launched();
     PS_TRY(cudaGetLastError());
     PS_TRY(cudaStreamSynchronize(p->stream));
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_prescreen_fit_norm(cui_prescreen p, const float *feat_dev, int64_t count)
+{
+    if (!p || !feat_dev || count < 1) return ps_fail(CUI_ERR_ARG, "bad arguments");
+    k_ps_fit_norm<<<p->desc.bands, 256, 0, p->stream>>>(feat_dev, count, p->desc.bands, p->frames, p->d_norm);
+    launched();
+    PS_TRY(cudaGetLastError());
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_prescreen_set_norm(cui_prescreen p, const float *mean, const float *stddev)
+{
+    if (!p || !mean || !stddev) return ps_fail(CUI_ERR_ARG, "bad arguments");
+    const int B = p->desc.bands;
+    std::vector<float> h(2 * B);
+    for (int b = 0; b < B; ++b) {
+        if (!std::isfinite(mean[b]) || !(stddev[b] > 0.f) || !std::isfinite(stddev[b]))
+            return ps_fail(CUI_ERR_ARG, "mean must be finite and stddev finite and > 0");
+        h[b] = mean[b];
+        h[B + b] = 1.f / stddev[b];
+    }
+    PS_TRY(cudaMemcpyAsync(p->d_norm, h.data(), sizeof(float) * 2 * B, cudaMemcpyHostToDevice, p->stream));
+    PS_TRY(cudaStreamSynchronize(p->stream));
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_prescreen_get_norm(cui_prescreen p, float *mean, float *stddev)
+{
+    if (!p || !mean || !stddev) return ps_fail(CUI_ERR_ARG, "bad arguments");
+    const int B = p->desc.bands;
+    std::vector<float> h(2 * B);
+    PS_TRY(cudaMemcpyAsync(h.data(), p->d_norm, sizeof(float) * 2 * B, cudaMemcpyDeviceToHost, p->stream));
+    PS_TRY(cudaStreamSynchronize(p->stream));
+    for (int b = 0; b < B; ++b) {
+        mean[b] = h[b];
+        stddev[b] = 1.f / h[B + b];
+    }
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_prescreen_ensemble_scores(const cui_prescreen *nets, int32_t k, const float *feat_dev,
+                                                    int64_t count, float *prob_dev)
+{
+    if (!nets || k < 1 || !feat_dev || !prob_dev || count < 0) return ps_fail(CUI_ERR_ARG, "bad arguments");
+    for (int32_t e = 0; e < k; ++e) {
+        if (!nets[e]) return ps_fail(CUI_ERR_ARG, "a network handle is NULL");
+        const cui_prescreen_desc &d = nets[e]->desc;
+        if (d.bands != nets[0]->desc.bands || nets[e]->frames != nets[0]->frames || d.regions != nets[0]->desc.regions)
+            return ps_fail(CUI_ERR_ARG, "the networks differ in bands, frames or regions");
+    }
+    cui_prescreen p0 = nets[0];
+    const int R = p0->desc.regions;
+    const int64_t row = (int64_t)p0->desc.bands * p0->frames;
+    // every network runs on the first one's stream, into its scratch, in chunks of its max_batch
+    for (int64_t s0 = 0; s0 < count; s0 += p0->desc.max_batch) {
+        const int c = (int)std::min<int64_t>(p0->desc.max_batch, count - s0);
+        for (int32_t e = 0; e < k; ++e) {
+            cui_prescreen p = nets[e];
+            PsArgs a = {p->d_w, p->d_norm, p->L};
+            PS_TRY(cudaFuncSetAttribute(k_ps_net, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps_net_smem(p->L)));
+            if (e > 0 && p->stream != p0->stream) PS_TRY(cudaStreamSynchronize(p->stream)); // its own pending work
+            k_ps_net<<<c, PS_NT, ps_net_smem(p->L), p0->stream>>>(a, feat_dev + s0 * row, nullptr, p0->d_logits,
+                                                                  nullptr, nullptr);
+            k_ps_softmax_mean<<<(c + 7) / 8, 256, 0, p0->stream>>>(p0->d_logits, c, R, 1.f / (float)k, e == 0,
+                                                                 prob_dev + s0 * R);
+            launched(2);
+        }
+    }
+    PS_TRY(cudaGetLastError());
     return CUI_OK;
 }
 

@@ -6,9 +6,9 @@ directly at the detection's time on the whole segment (or on a decimated copy
 of its lower band), and the two bands are added coherently.
 
 Every step is a library call (cui_segment_band_series, cui_bank_set_band,
-cui_filter_bank, cui_triggers, cui_band_correlate); this module only cuts the
-device series into segments and combines the returned sums:
-rho = |z_high + z_low| / sqrt(sigma_high^2 + sigma_low^2).
+cui_filter_bank, cui_triggers, cui_band_combine); this module only cuts the
+device series into segments and gathers the candidates.  The combination
+rho = |z_high + z_low| / sqrt(sigma_high^2 + sigma_low^2) runs in the library.
 """
 
 from __future__ import annotations
@@ -70,19 +70,15 @@ def hierarchical_search(segment, detect, f_split: float, psd_short, low=None):
         trig = trig[(trig["sample"] + s0 >= first) & (trig["sample"] + s0 < end)]
         if len(trig) == 0:
             continue
-        zh, s2h = detect.band_correlate(trig["tmpl"], trig["sample"] / fs, f_split, 0.0)
         rec = np.zeros(len(trig), dtype=CANDIDATE_DTYPE)
         rec["tmpl"] = trig["tmpl"]
         rec["t"] = (s0 + trig["sample"]) / fs
         rec["rho_high"] = trig["snr"]
-        parts.append((rec, zh, s2h))
+        # completed while this short segment is still the detect bank's
+        rec["rho"], rec["phase"], _ = detect.band_combine(trig["sample"] / fs, segment if low is None else low,
+                                                          rec["t"], rec["tmpl"], f_split)
+        parts.append(rec)
     if not parts:
         return np.zeros(0, dtype=CANDIDATE_DTYPE)
-    rec = np.concatenate([p[0] for p in parts])
-    zh = np.concatenate([p[1] for p in parts])
-    s2h = np.concatenate([p[2] for p in parts])
-    zl, s2l = (segment if low is None else low).band_correlate(rec["tmpl"], rec["t"], 0.0, f_split)
-    z = zh + zl
-    rec["rho"] = np.abs(z) / np.sqrt(s2h + s2l)
-    rec["phase"] = np.angle(z)
+    rec = np.concatenate(parts)
     return rec[np.argsort(rec["t"], kind="stable")]

@@ -16,25 +16,18 @@ its own :class:`Bank` on its own GPU.
 
 from __future__ import annotations
 
-import math
-
 import numpy as np
 
 from .regions import chirp_mass
 
-MSUN_S = 4.925490947e-6  # G M_sun / c^3 in seconds
-
 
 def band_bins(m1, m2, *, n: int, fs: float, f_low: float):
-    """k_hi - k_low per template: k_low = ceil(f_low / df) and
-    k_hi = min(ceil(f_isco / df), N/2) with f_isco = 1 / (6^(3/2) pi M)."""
-    m1 = np.asarray(m1, dtype=np.float64)
-    m2 = np.asarray(m2, dtype=np.float64)
-    df = fs / n
-    f_isco = 1.0 / (6.0 ** 1.5 * math.pi * (m1 + m2) * MSUN_S)
-    k_lo = math.ceil(f_low / df)
-    k_hi = np.minimum(np.ceil(f_isco / df), n // 2)
-    return np.maximum(k_hi - k_lo, 0.0)
+    """k_hi - k_low per template, by the library's own band rule
+    (cui_template_bands, host code; no GPU needed)."""
+    from . import template_bands
+
+    k_lo, k_hi = template_bands(m1, m2, n=n, fs=fs, f_low=f_low)
+    return np.maximum(k_hi.astype(np.float64) - k_lo, 0.0)
 
 
 def template_cost(m1, m2, *, n: int, fs: float, f_low: float, band_weight: float = 0.5):

@@ -2,19 +2,27 @@
 a GPU machine; not collected by pytest):
 
     python tests/prescreen_config4.py [--train 200000] [--test 1000] [--epochs 20] [--bands 16] [--frame 256]
-                                      [--seed 1] [--ensemble 3]
+                                      [--seed 1] [--ensemble 3] [--labels region|response] [--out FILE]
 
 The network is trained on the GPU with oracle-made injections (one per 16 s
 segment, N = 2^16 at 4096 Hz, SNR uniform in [6, 20], masses log-uniform in
-[1, 25] Msun, 3.5PN, f_low 20 Hz), labelled with the region (1 of 100
+[1, 25] Msun, 3.5PN, f_low 20 Hz).  Labels: `region` is the region (1 of 100
 equal-count chirp-mass groups of the 10^4-template bank) of the injected
-chirp mass.  On held-out segments the exhaustive bank is compared with
+chirp mass, 0.5 on its two neighbours; `response` is the bank's own response
+to the segment: the regions whose templates trigger at rho >= 8 within 1 s of
+the injection (uniform over them), the region label where none does.  The
+response is computed by the exhaustive GPU bank (parity-tested against the
+oracle) for every training segment, and checked against the FP64 oracle's
+response on the first 512 segments
+(tests/prescreen_labels/oracle_response_seed4.npz, written by
+make_oracle_labels.py there).  On held-out segments the exhaustive bank is compared with
 filtering only the top-K scored regions: K* is the smallest K with zero missed
 injections among those the exhaustive bank detects at rho >= 8 (a miss: no
 template of the top-K regions reaches rho >= 8 within 1 s of the injection),
 and the speedup is the exhaustive time over prescreen + top-K* time.  Prints
 one JSON report; the same K* for an unranked (random) region order is the
-baseline without the network.
+baseline without the network, and K* of each network of the ensemble alone is
+reported next to the ensemble's.
 """
 
 from __future__ import annotations
@@ -50,6 +58,7 @@ def main():
     ap.add_argument("--seed", type=int, default=1, help="seed of the network initialisation")
     ap.add_argument("--ensemble", type=int, default=3,
                     help="networks trained from seeds seed, seed+1, ...; regions ranked by their mean probability")
+    ap.add_argument("--labels", default="region", choices=["region", "response"])
     args = ap.parse_args()
 
     import multiprocessing as mp
@@ -59,7 +68,7 @@ def main():
 
     import torch
 
-    from paper_1006_4644_gb300 import Bank, Prescreen, build, prescreen_rank
+    from paper_1006_4644_gb300 import Bank, Prescreen, build, ensemble_scores, prescreen_rank
 
     build.build()
     n, fs, f_low, R, W = 1 << 16, 4096.0, 20.0, 100, 4096
@@ -74,7 +83,20 @@ def main():
     ps_[0] = 1.0
     psd_d = torch.from_numpy(ps_).cuda()
     rep = {"n": n, "bands": args.bands, "frame": args.frame, "templates": len(m1), "regions": R, "train": args.train,
-           "test": args.test, "epochs": args.epochs, "seed": args.seed, "ensemble": args.ensemble}
+           "test": args.test, "epochs": args.epochs, "seed": args.seed, "ensemble": args.ensemble,
+           "labels": args.labels}
+
+    def region_response(bank, d, j0):
+        """Largest trigger rho of each region within W samples of j0 (circular)."""
+        bank.upload(synth.strain_from_spectrum(d, n, fs), psd)
+        bank.filter()
+        tr, _ = bank.triggers()
+        dist = np.abs(tr["sample"] - j0)
+        near = tr[np.minimum(dist, n - dist) <= W]
+        reg = np.zeros(R)
+        if len(near):
+            np.maximum.at(reg, region_of_tmpl[near["tmpl"]], near["snr"])
+        return reg
 
     import contextlib
 
@@ -85,21 +107,25 @@ def main():
         p = nets[0]  # the features do not depend on the network
 
         def score(x, out):
-            """Mean over the networks of the region probabilities."""
-            acc = None
-            for net in nets:
-                net.scores(x, out)
-                pr = torch.softmax(out, dim=1)
-                acc = pr if acc is None else acc + pr
-            out.copy_(acc / len(nets))
+            """Mean over the networks of the region probabilities (in the library)."""
+            ensemble_scores(nets, x, out)
 
-        def feats(start, count, keep_meta=False):
+        def feats(start, count, keep_meta=False, label_bank=None, responses=None):
             X, Y, M, D = [], [], [], []
             for s0 in range(start, start + count, 2048):
                 d, y, meta = make_segments_mp(4, s0, min(2048, start + count - s0), n, fs, f_low, psd, bounds, R,
                                               pool=pool)
                 out = torch.zeros((len(d), p.bands, p.frames), dtype=torch.float32, device="cuda")
                 p.features(torch.from_numpy(d).cuda(), psd_d, out)
+                if label_bank is not None:
+                    for i in range(len(d)):
+                        reg = region_response(label_bank, d[i], meta[i]["j0"])
+                        if responses is not None and len(responses) < 512:
+                            responses.append(reg)
+                        hit = reg >= 8.0
+                        if hit.any():
+                            y[i] = hit / hit.sum()
+                            hits.append(int(hit.sum()))
                 X.append(out)
                 Y.append(torch.from_numpy(y).cuda())
                 M += meta
@@ -108,10 +134,29 @@ def main():
             return torch.cat(X), torch.cat(Y), M, (np.concatenate(D) if keep_meta else None)
 
         t0 = time.perf_counter()
-        xtr, ytr, _, _ = feats(0, args.train)
+        hits = []  # regions responding at rho >= 8, per training segment that has any
+        if args.labels == "response":
+            responses = []
+            with Bank(m1, m2, n=n, fs=fs, f_low=f_low, pn_x2=7, snr_threshold=6.0, window=W) as lb:
+                xtr, ytr, _, _ = feats(0, args.train, label_bank=lb, responses=responses)
+            rep["labels_response"] = {"segments_with_a_response": len(hits),
+                                      "mean_regions_responding": float(np.mean(hits)) if hits else 0.0}
+            path = os.path.join(ROOT, "tests", "prescreen_labels", "oracle_response_seed4.npz")
+            if os.path.exists(path):
+                ref = np.load(path)["response"].astype(np.float64)
+                got = np.array(responses[:len(ref)])
+                ref = ref[:len(got)]
+                both = (ref > 0) & (got > 0)
+                rep["labels_vs_oracle"] = {
+                    "segments": int(len(got)),
+                    "hit_sets_equal": int(np.sum(np.all((ref >= 8.0) == (got >= 8.0), axis=1))),
+                    "max_rel_err_rho": float(np.max(np.abs(got[both] / ref[both] - 1.0))) if both.any() else None,
+                    "regions_with_a_trigger_in_one_only": int(np.sum((ref > 0) != (got > 0)))}
+        else:
+            xtr, ytr, _, _ = feats(0, args.train)
         rep["data_s"] = time.perf_counter() - t0
-        mu, sd = xtr.mean(dim=(0, 2), keepdim=True), xtr.std(dim=(0, 2), keepdim=True)
-        xtr = ((xtr - mu) / sd).contiguous()
+        for net in nets:  # per-band standardisation, kept in each network's state
+            net.fit_norm(xtr)
         t0 = time.perf_counter()
         losses = []
         for net in nets:
@@ -132,38 +177,37 @@ def main():
         rep["loss_by_epoch"] = losses
 
         xte, yte, meta, dte = feats(10_000_000, args.test, keep_meta=True)
-        xte = ((xte - mu) / sd).contiguous()
         scores = torch.zeros((len(xte), R), dtype=torch.float32, device="cuda")
         score(xte, scores)
         sc = scores.cpu().numpy()
         true = yte.argmax(dim=1).cpu().numpy()
         rep["recall_at"] = {k: float(np.mean([t in np.argsort(-s)[:k] for t, s in zip(true, sc)]))
                             for k in (1, 5, 10, 20, 50)}
+        single = []  # each network's own scores, for its K* alone
+        for net in nets:
+            z = torch.zeros((len(xte), R), dtype=torch.float32, device="cuda")
+            net.scores(xte, z)
+            single.append(z.cpu().numpy())
 
         # exhaustive bank on every held-out segment: region maxima of rho near the injection
         rng = np.random.default_rng(0)
         k_net, k_rand, detectable = [], [], 0
+        k_single = [[] for _ in nets]
         with Bank(m1, m2, n=n, fs=fs, f_low=f_low, pn_x2=7, snr_threshold=6.0, window=W) as bank:
             for i, mt in enumerate(meta):
-                strain = synth.strain_from_spectrum(dte[i], n, fs)
-                bank.upload(strain, psd)
-                bank.filter()
-                tr, _ = bank.triggers()
-                dist = np.abs(tr["sample"] - mt["j0"])
-                dist = np.minimum(dist, n - dist)
-                near = tr[dist <= W]
-                reg_max = np.zeros(R)
-                if len(near):
-                    np.maximum.at(reg_max, region_of_tmpl[near["tmpl"]], near["snr"])
+                reg_max = region_response(bank, dte[i], mt["j0"])
                 if reg_max.max() < 8.0:
                     continue
                 detectable += 1
                 hit = reg_max >= 8.0
                 k_net.append(int(np.argmax(hit[np.argsort(-sc[i], kind="stable")])) + 1)
                 k_rand.append(int(np.argmax(hit[rng.permutation(R)])) + 1)
+                for e, z in enumerate(single):
+                    k_single[e].append(int(np.argmax(hit[np.argsort(-z[i], kind="stable")])) + 1)
             rep["detectable"] = detectable
             k_star = int(max(k_net)) if k_net else R
             rep["K_star"] = k_star
+            rep["K_star_per_network"] = {str(args.seed + e): (int(max(k)) if k else R) for e, k in enumerate(k_single)}
             rep["K_star_random_order"] = int(max(k_rand)) if k_rand else R
             rep["K_median"] = float(np.median(k_net)) if k_net else None
             rep["K_median_random_order"] = float(np.median(k_rand)) if k_rand else None
@@ -185,8 +229,7 @@ def main():
                 bank.filter()
                 ev[1].record(stream)
                 p.bank_features(bank, feat1)
-                feat_n = ((feat1 - mu) / sd).contiguous()
-                score(feat_n, sc1)
+                score(feat1, sc1)
                 order = prescreen_rank(m1, m2, sc1.cpu().numpy()[0], k_star)
                 bank.filter(order)
                 ev[2].record(stream)
@@ -204,7 +247,7 @@ def main():
                 ev[0].record(stream)
                 for _ in range(reps):
                     p.bank_features(bank, feat1)
-                    score(((feat1 - mu) / sd).contiguous(), sc1)
+                    score(feat1, sc1)
                     bank.filter(order)
                 ev[1].record(stream)
                 torch.cuda.synchronize()

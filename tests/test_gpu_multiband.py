@@ -93,6 +93,49 @@ def test_band_filter_at_2p20_sampled():
     assert not rep.errors, rep.errors[:5]
 
 
+def test_band_combine_matches_the_oracle():
+    """cui_band_combine: the upper band on one bank and the lower band on
+    another, added coherently in the library, against the oracle's direct band
+    sums combined as rho = |z_h + z_l| / sqrt(sigma_h^2 + sigma_l^2); with both
+    banks on the same segment and time, the split bands make up the full band,
+    so rho is the filter's own peak; its per-band sums are those
+    cui_band_correlate returns."""
+    from paper_1006_4644_gb300 import Bank, CuiError, _lib
+
+    w = W16
+    strain, psd, dt, (tmpl, j0, _) = make_segment(w)
+    m1, m2 = w.masses()
+    f_split = 70.0
+    with _bank(w) as hb, _bank(w) as lb:
+        hb.upload(strain, psd)
+        lb.upload(strain, psd)
+        hb.filter()
+        pk = hb.peaks()
+        tm = np.unique(np.concatenate([np.arange(0, w.n_templates, 5), tmpl])).astype(np.int32)
+        ts = pk["sample"][tm] / w.fs
+        rho, ph, sums = hb.band_combine(ts, lb, ts, tm, f_split)
+        zh, s2h = hb.band_correlate(tm, ts, f_split, 0.0)
+        zl, s2l = lb.band_correlate(tm, ts, 0.0, f_split)
+        assert np.array_equal(sums[:, 0] + 1j * sums[:, 1], zh) and np.array_equal(sums[:, 2], s2h)
+        assert np.array_equal(sums[:, 3] + 1j * sums[:, 4], zl) and np.array_equal(sums[:, 5], s2l)
+        assert np.max(np.abs(rho / pk["snr"][tm] - 1.0)) < 1e-3
+        with pytest.raises(CuiError) as e:
+            hb.band_combine(ts, lb, ts, tm, 0.0)
+        assert e.value.status == _lib.CUI_ERR_ARG
+        with Bank(m1[::-1].copy(), m2[::-1].copy(), n=w.n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2) as other:
+            other.upload(strain, psd)
+            with pytest.raises(CuiError) as e:
+                hb.band_combine(ts, other, ts, tm, f_split)
+            assert e.value.status == _lib.CUI_ERR_ARG
+    for i, t in enumerate(tm):
+        a, sa = oracle.band_correlate(dt, psd, m1[t], m2[t], w.pn_x2, w.f_low, w.fs, w.n, [ts[i]], f_split, 0.0)
+        b, sb = oracle.band_correlate(dt, psd, m1[t], m2[t], w.pn_x2, w.f_low, w.fs, w.n, [ts[i]], 0.0, f_split)
+        z = a[0] + b[0]
+        want = abs(z) / math.sqrt(sa + sb)
+        assert abs(rho[i] - want) <= 1e-3 * want, (t, rho[i], want)
+        assert abs((ph[i] - np.angle(z) + math.pi) % (2 * math.pi) - math.pi) < 2e-3
+
+
 @pytest.mark.parametrize("ccols", [16, 32, 64])
 def test_band_correlate_matches_the_oracle(ccols):
     """Bins are generated in blocks of `ccols` (the pass-1 tiling), so every

@@ -66,6 +66,94 @@ def test_gradients_match_the_oracle():
     assert np.max(np.abs(got - want)) <= 1e-2 * np.max(np.abs(want))
 
 
+def test_adam_steps_match_the_oracle():
+    """Three training steps: each step's parameters and moments against the
+    FP64 Adam step (oracle.prescreen.adam_step) applied to the state before it
+    and to the batch gradient, which cui_prescreen_gradient returns without
+    updating (the step recomputes the same gradient, deterministically)."""
+    import torch
+
+    rng = np.random.default_rng(12)
+    lr, b1, b2, eps = 2e-3, 0.9, 0.999, 1e-8
+    with _ps(lr=lr, seed=5) as p:
+        g = torch.zeros(p.n_params, dtype=torch.float32, device="cuda")
+        for step in range(3):
+            x = torch.from_numpy(rng.standard_normal((8, 8, p.frames)).astype(np.float32)).cuda()
+            y = torch.from_numpy(np.stack([ops.soft_labels(int(r)) for r in rng.integers(0, 100, 8)])
+                                 .astype(np.float32)).cuda()
+            th0, m0, v0, st0 = p.get_state()
+            assert st0 == step
+            p.gradient(x, y, g)
+            p.train_step(x, y, want_loss=False)
+            th1, m1, v1, st1 = p.get_state()
+            assert st1 == step + 1
+            # the handle keeps lr, beta1, beta2 and eps as FP32 values: the oracle takes the same numbers
+            f32 = [float(np.float32(c)) for c in (lr, b1, b2, eps)]
+            want_th, want_m, want_v = ops.adam_step(th0, m0, v0, g.cpu().numpy(), st1, *f32)
+            # FP32 rounding of b m + (1 - b) g is bounded by the size of its terms
+            # (they can cancel), not by the result
+            gh = g.cpu().numpy().astype(np.float64)
+            m_terms = np.abs(f32[1] * m0) + np.abs((1 - f32[1]) * gh)
+            v_terms = np.abs(f32[2] * v0) + np.abs((1 - f32[2]) * gh * gh)
+            assert np.all(np.abs(m1 - want_m) <= 1e-6 * m_terms + 1e-30)
+            assert np.all(np.abs(v1 - want_v) <= 1e-6 * v_terms + 1e-30)
+            assert np.all(np.abs(th1 - want_th) <= 4e-6 * lr + 2.0 ** -22 * np.abs(want_th)), step
+            assert np.max(np.abs(th1 - th0)) > 0.5 * lr  # the step moved the parameters
+
+
+def test_standardisation_matches_the_oracle():
+    """cui_prescreen_fit_norm against the oracle's per-band mean and standard
+    deviation, and the network's gradient with the standardisation applied
+    inside the kernel against the oracle's gradient of standardised inputs."""
+    import torch
+
+    rng = np.random.default_rng(21)
+    with _ps() as p:
+        f = (rng.standard_normal((40, 8, p.frames)) * np.linspace(0.5, 3.0, 8)[None, :, None]
+             + np.linspace(-4.0, 2.0, 8)[None, :, None]).astype(np.float32)
+        fd = torch.from_numpy(f).cuda()
+        p.fit_norm(fd)
+        mean, sd = p.get_norm()
+        wm, wsd = ops.fit_norm(f.astype(np.float64))
+        assert np.max(np.abs(mean - wm)) < 1e-5 and np.max(np.abs(sd / wsd - 1.0)) < 1e-5
+        x, yv = f[:6], np.stack([ops.soft_labels(int(r)) for r in rng.integers(0, 100, 6)]).astype(np.float32)
+        g = torch.zeros(p.n_params, dtype=torch.float32, device="cuda")
+        p.gradient(fd[:6].contiguous(), torch.from_numpy(yv).cuda(), g)
+        theta = bf16_round(p.get_state()[0])
+    xs = [ops.standardise(r, mean.astype(np.float64), sd.astype(np.float64)) for r in x.astype(np.float64)]
+    want = ops.gradient(theta, xs, list(yv.astype(np.float64)))
+    got = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - want) <= 2e-3 * np.linalg.norm(want)
+
+
+def test_ensemble_scores_match_the_oracle():
+    """cui_prescreen_ensemble_scores: the mean of the softmax probabilities of
+    three networks, each with its own standardisation, against the oracle's
+    forward passes with the same (BF16-rounded) parameters."""
+    import torch
+
+    from paper_1006_4644_gb300 import ensemble_scores
+
+    rng = np.random.default_rng(33)
+    nets = [_ps(seed=s, max_batch=4) for s in (1, 2, 3)]
+    try:
+        for i, q in enumerate(nets):
+            q.set_norm(np.linspace(-1.0, 1.0, 8) * i, np.linspace(0.5, 2.0, 8) + i)
+        x = rng.standard_normal((10, 8, nets[0].frames)).astype(np.float32)  # 10 rows: chunks of max_batch 4
+        out = torch.zeros((10, 100), dtype=torch.float32, device="cuda")
+        ensemble_scores(nets, torch.from_numpy(x).cuda(), out)
+        got = out.cpu().numpy()
+        params = [(bf16_round(q.get_state()[0]), *q.get_norm()) for q in nets]
+    finally:
+        for q in nets:
+            q.close()
+    for r in range(10):
+        logits = [ops.forward(th, ops.standardise(x[r].astype(np.float64), mu.astype(np.float64),
+                                                  sd.astype(np.float64)))[0] for th, mu, sd in params]
+        want = ops.ensemble_probabilities(logits)
+        assert np.max(np.abs(got[r] - want)) < 1e-4 and abs(got[r].sum() - 1.0) < 1e-5
+
+
 def test_training_is_deterministic_and_resumable(tmp_path):
     import torch
 
@@ -85,9 +173,14 @@ def test_training_is_deterministic_and_resumable(tmp_path):
     with _ps(seed=7) as c:
         for x, y in batches[:3]:
             c.train_step(x, y)
+        c.set_norm(np.full(8, 0.25), np.full(8, 1.5))
         c.save(str(tmp_path / "ck.bin"))
+        c.set_norm(np.zeros(8), np.ones(8))
+        c.load(str(tmp_path / "ck.bin"))  # the checkpoint carries the standardisation
+        assert np.allclose(c.get_norm()[0], 0.25) and np.allclose(c.get_norm()[1], 1.5)
     with _ps(seed=99) as d:
         d.load(str(tmp_path / "ck.bin"))
+        d.set_norm(np.zeros(8), np.ones(8))
         for x, y in batches[3:]:
             d.train_step(x, y)
         sd = d.get_state()
@@ -95,51 +188,102 @@ def test_training_is_deterministic_and_resumable(tmp_path):
 
 
 def test_trained_prescreen_beats_unranked_regions():
-    """After training on oracle-made injections, the true region of held-out
-    injections sits in the top 20 of 100 scored regions far more often than
-    the 20 % an unranked (random) order gives."""
+    """Train -> score -> rank -> filter, every step through the C ABI.  Two
+    networks are trained on oracle-made injections with the library's own
+    feature standardisation (cui_prescreen_fit_norm); their ensemble scores
+    (cui_prescreen_ensemble_scores) put the true region of held-out injections
+    in the top 20 of 100 regions far more often than the 20 % an unranked
+    order gives.  On held-out segments the exhaustive bank then fixes K*, the
+    fewest top-scored regions that miss none of the injections it detects at
+    rho >= 8 within 1 s; filtering only those regions (cui_prescreen_rank ->
+    cui_filter_bank with that order) finds each of them, with the same triggers
+    the exhaustive bank gives for those templates."""
     import torch
 
-    n, fs, f_low, R = 1 << 16, 4096.0, 20.0, 100
+    from paper_1006_4644_gb300 import Bank, ensemble_scores, prescreen_rank
+
+    n, fs, f_low, R, W = 1 << 16, 4096.0, 20.0, 100, 4096
     psd = synth.psd_onesided(n, fs)
     bank = synth.WORKLOADS["seg256s_bank10k_pn35"]
-    groups, bounds = ops.regions_of_bank(*bank.masses(), R)
+    m1, m2 = bank.masses()
+    groups, bounds = ops.regions_of_bank(m1, m2, R)
+    region_of_tmpl = np.empty(len(m1), dtype=np.int64)
+    for r, gr in enumerate(groups):
+        region_of_tmpl[gr] = r
     ps_ = psd.copy()
     ps_[0] = 1.0
     psd_d = torch.from_numpy(ps_).cuda()
-    with _ps(n=n, frame=512, max_batch=128, lr=2e-3, seed=1) as p:
+    nets = [_ps(n=n, frame=512, max_batch=128, lr=2e-3, seed=s) for s in (1, 2)]
+    try:
+        p = nets[0]
 
-        def feats(start, count):
-            X, Y = [], []
+        def feats(start, count, keep=False):
+            X, Y, D, M = [], [], [], []
             for s0 in range(start, start + count, 256):
-                d, y, _ = make_segments(2024, s0, min(256, start + count - s0), n, fs, f_low, psd, bounds, R)
+                d, y, meta = make_segments(2024, s0, min(256, start + count - s0), n, fs, f_low, psd, bounds, R)
                 out = torch.zeros((len(d), 8, p.frames), dtype=torch.float32, device="cuda")
                 p.features(torch.from_numpy(d).cuda(), psd_d, out)
                 X.append(out)
                 Y.append(torch.from_numpy(y).cuda())
-            return torch.cat(X), torch.cat(Y)
+                if keep:
+                    D.append(d)
+                    M += meta
+            return torch.cat(X), torch.cat(Y), (np.concatenate(D) if keep else None), M
 
-        xtr, ytr = feats(0, 16384)
-        xte, yte = feats(1_000_000, 1024)
-        mu, sd = xtr.mean(dim=(0, 2), keepdim=True), xtr.std(dim=(0, 2), keepdim=True)
-        xtr, xte = (xtr - mu) / sd, (xte - mu) / sd
+        xtr, ytr, _, _ = feats(0, 16384)
+        xte, yte, dte, meta = feats(1_000_000, 1024, keep=True)
+        for q in nets:
+            q.fit_norm(xtr)
         true = yte.argmax(dim=1).cpu().numpy()
 
         def recall20():
-            scores = torch.zeros((len(xte), R), dtype=torch.float32, device="cuda")
-            p.scores(xte.contiguous(), scores)
-            top = torch.topk(scores, 20, dim=1).indices.cpu().numpy()
-            return float(np.mean([t in row for t, row in zip(true, top)]))
+            probs = torch.zeros((len(xte), R), dtype=torch.float32, device="cuda")
+            ensemble_scores(nets, xte, probs)
+            top = torch.topk(probs, 20, dim=1).indices.cpu().numpy()
+            return float(np.mean([t in row for t, row in zip(true, top)])), probs.cpu().numpy()
 
-        before = recall20()
-        g = torch.Generator(device="cpu").manual_seed(0)
-        for epoch in range(16):
-            perm = torch.randperm(len(xtr), generator=g)
-            for i in range(0, len(xtr) - 127, 128):
-                idx = perm[i:i + 128].cuda()
-                p.train_step(xtr[idx].contiguous(), ytr[idx].contiguous(), want_loss=False)
-        after = recall20()
-    # an unranked order puts the true region in the top 20 with probability 0.2
-    # (standard error 0.0125 over 1024 segments); the untrained network is no better
-    print(f"recall@20: untrained {before:.3f}, trained {after:.3f}")
-    assert after > 0.3 and after > before + 0.08, (before, after)
+        before, _ = recall20()
+        for q in nets:
+            g = torch.Generator(device="cpu").manual_seed(0)
+            for epoch in range(16):
+                perm = torch.randperm(len(xtr), generator=g)
+                for i in range(0, len(xtr) - 127, 128):
+                    idx = perm[i:i + 128].cuda()
+                    q.train_step(xtr[idx].contiguous(), ytr[idx].contiguous(), want_loss=False)
+        after, probs = recall20()
+        # an unranked order puts the true region in the top 20 with probability 0.2
+        # (standard error 0.0125 over 1024 segments); the untrained networks are no better
+        print(f"recall@20: untrained {before:.3f}, trained {after:.3f}")
+        assert after > 0.3 and after > before + 0.08, (before, after)
+
+        # held-out segments judged by the exhaustive bank
+        with Bank(m1, m2, n=n, fs=fs, f_low=f_low, pn_x2=7, snr_threshold=6.0, window=W) as b:
+            cases = []
+            for i in range(64):
+                b.upload(synth.strain_from_spectrum(dte[i], n, fs), psd)
+                b.filter()
+                tr, _ = b.triggers()
+                dist = np.abs(tr["sample"] - meta[i]["j0"])
+                near = tr[np.minimum(dist, n - dist) <= W]
+                reg = np.zeros(R)
+                if len(near):
+                    np.maximum.at(reg, region_of_tmpl[near["tmpl"]], near["snr"])
+                if reg.max() >= 8.0:
+                    k = int(np.argmax((reg >= 8.0)[np.argsort(-probs[i], kind="stable")])) + 1
+                    cases.append((i, tr, k))
+            assert len(cases) >= 10, len(cases)
+            k_star = max(k for _, _, k in cases)
+            for i, tr_full, _ in cases:
+                order = prescreen_rank(m1, m2, probs[i], k_star)
+                assert len(order) == sum(len(groups[r]) for r in np.argsort(-probs[i], kind="stable")[:k_star])
+                b.upload(synth.strain_from_spectrum(dte[i], n, fs), psd)
+                b.filter(order)
+                tr, _ = b.triggers()
+                keep = np.isin(tr_full["tmpl"], order)
+                assert np.array_equal(tr, tr_full[keep]), i
+                dist = np.abs(tr["sample"] - meta[i]["j0"])
+                assert np.any((np.minimum(dist, n - dist) <= W) & (tr["snr"] >= 8.0)), i
+        print(f"K* on {len(cases)} detectable held-out injections: {k_star} of {R} regions")
+    finally:
+        for q in nets:
+            q.close()

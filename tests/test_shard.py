@@ -83,3 +83,25 @@ def test_two_gloo_ranks_gather_the_single_process_result(tmp_path):
     assert int(got["total"]) == ref_total
     s0, s1 = got["shard0"], got["shard1"]
     assert len(s0) and len(s1) and len(np.intersect1d(s0, s1)) == 0
+
+
+def test_library_band_rule_matches_the_oracle_and_clamps():
+    """cui_template_bands (host code, no GPU) gives the oracle's template
+    support [k_low, k_hi) for random masses, and clamps k_low at N/2 when
+    f_low reaches Nyquist (every band empty)."""
+    from paper_1006_4644_gb300 import CuiError, template_bands
+
+    rng = np.random.default_rng(17)
+    m1, m2 = rng.uniform(1.0, 60.0, 40), rng.uniform(1.0, 60.0, 40)
+    for n, f_low in [(1 << 12, 30.0), (1 << 16, 10.0), (1 << 20, 20.0)]:
+        k_lo, k_hi = template_bands(m1, m2, n=n, fs=4096.0, f_low=f_low)
+        for t in range(len(m1)):
+            _, lo, hi = oracle.spa_template(m1[t], m2[t], 7, f_low, 4096.0, n)
+            if hi > lo:
+                assert (k_lo, int(k_hi[t])) == (lo, hi)
+            else:
+                assert int(k_hi[t]) <= k_lo
+    k_lo, _ = template_bands([1.4], [1.4], n=1 << 12, fs=4096.0, f_low=1e300)
+    assert k_lo == 1 << 11
+    with pytest.raises(CuiError):
+        template_bands([1.4], [-1.0], n=1 << 12, fs=4096.0, f_low=20.0)
