@@ -480,6 +480,20 @@ cui_status cui_prescreen_ensemble_scores(const cui_prescreen *nets, int32_t k, c
 cui_status cui_prescreen_rank(const double *m1, const double *m2, int64_t n_templates, const float *scores,
                               int32_t regions, int32_t top_k, int32_t *order_out, int64_t *n_out);
 
+/* The same ranking with the bank's chirp-mass order computed once: create
+ * keeps the bank points sorted and cut into `regions` groups (the rules of
+ * cui_prescreen_rank; host arrays, copied), order writes the template order
+ * of the top_k best-scored regions exactly as cui_prescreen_rank would, in
+ * O(regions log regions + templates written) per call, destroy frees the plan
+ * (NULL allowed).  Host only, no GPU.  Errors: CUI_ERR_ARG.  Paper: as
+ * cui_prescreen_rank; the plan itself is not in the paper. */
+typedef struct cui_regions_s *cui_regions;
+cui_status cui_regions_create(const double *m1, const double *m2, int64_t n_templates, int32_t regions,
+                              cui_regions *out);
+cui_status cui_regions_order(cui_regions plan, const float *scores, int32_t top_k, int32_t *order_out,
+                             int64_t *n_out);
+void cui_regions_destroy(cui_regions plan);
+
 /* Allocation-free normalisation: sigma_t^2 = 4 df sum_k |h~_k|^2 / S_k of
  * `count` templates (m1[t], m2[t], host arrays, read during the call) for the
  * one-sided PSD psd_dev (N/2 + 1 FP64 values in device memory, read on

@@ -22,7 +22,7 @@ from . import _lib
 from ._lib import (CUI_PLAIN, CUI_PLAIN_FP64, CUI_PSI_FP64, CUI_STORE_BF16, PEAK_DTYPE, TRIGGER_DTYPE, CuiError,
                    cui_bank_desc)
 
-__all__ = ["Bank", "Prescreen", "prescreen_rank", "ensemble_scores", "template_bands", "CuiError", "CUI_PSI_FP64", "CUI_STORE_BF16", "CUI_PLAIN",
+__all__ = ["Bank", "Prescreen", "Regions", "prescreen_rank", "ensemble_scores", "template_bands", "CuiError", "CUI_PSI_FP64", "CUI_STORE_BF16", "CUI_PLAIN",
            "CUI_PLAIN_FP64", "PEAK_DTYPE", "TRIGGER_DTYPE", "load"]
 
 load = _lib.load
@@ -288,6 +288,51 @@ def prescreen_rank(m1, m2, scores, top_k: int | None = None):
     _lib.check(lib.cui_prescreen_rank(m1.ctypes.data, m2.ctypes.data, len(m1), sc.ctypes.data, regions, k,
                                       out.ctypes.data, C.byref(cnt)), "cui_prescreen_rank")
     return out[: cnt.value].copy()
+
+
+class Regions:
+    """A bank's region plan (cui_regions_*): the bank sorted by chirp mass and
+    cut into equal-count regions once; order(scores, top_k) is then the
+    template order of the top_k best-scored regions, as prescreen_rank gives."""
+
+    def __init__(self, m1, m2, regions: int = 100):
+        self._l = _lib.load_prescreen(_lib.load())
+        a1 = np.ascontiguousarray(m1, dtype=np.float64)
+        a2 = np.ascontiguousarray(m2, dtype=np.float64)
+        if a1.shape != a2.shape:
+            raise ValueError("m1 and m2 must have the same length")
+        h = C.c_void_p()
+        _lib.check(self._l.cui_regions_create(a1.ctypes.data, a2.ctypes.data, len(a1), int(regions), C.byref(h)),
+                   "cui_regions_create")
+        self._h, self.regions, self.n_templates = h, int(regions), len(a1)
+        self._out = np.empty(len(a1), dtype=np.int32)
+
+    def order(self, scores, top_k: int | None = None):
+        sc = np.ascontiguousarray(scores, dtype=np.float32)
+        if sc.shape != (self.regions,):
+            raise ValueError("one score per region")
+        cnt = C.c_int64()
+        k = self.regions if top_k is None else int(top_k)
+        _lib.check(self._l.cui_regions_order(self._h, sc.ctypes.data, k, self._out.ctypes.data, C.byref(cnt)),
+                   "cui_regions_order")
+        return self._out[:cnt.value].copy()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._l.cui_regions_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def template_bands(m1, m2, *, n: int, fs: float, f_low: float):

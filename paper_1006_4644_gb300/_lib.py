@@ -133,6 +133,10 @@ def load_prescreen(lib):
     lib.cui_prescreen_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_int64)]
     lib.cui_prescreen_set_state.argtypes = [vp, vp, vp, vp, C.c_int64]
     lib.cui_prescreen_rank.argtypes = [vp, vp, C.c_int64, vp, C.c_int32, C.c_int32, vp, C.POINTER(C.c_int64)]
+    lib.cui_regions_create.argtypes = [vp, vp, C.c_int64, C.c_int32, C.POINTER(vp)]
+    lib.cui_regions_order.argtypes = [vp, vp, C.c_int32, vp, C.POINTER(C.c_int64)]
+    lib.cui_regions_destroy.argtypes = [vp]
+    lib.cui_regions_destroy.restype = None
     lib.cui_prescreen_fit_norm.argtypes = [vp, vp, C.c_int64]
     lib.cui_prescreen_set_norm.argtypes = [vp, vp, vp]
     lib.cui_prescreen_get_norm.argtypes = [vp, vp, vp]
@@ -141,6 +145,6 @@ def load_prescreen(lib):
                  "cui_prescreen_scores", "cui_prescreen_train_step", "cui_prescreen_gradient",
                  "cui_prescreen_get_state", "cui_prescreen_set_state", "cui_prescreen_rank",
                  "cui_prescreen_fit_norm", "cui_prescreen_set_norm", "cui_prescreen_get_norm",
-                 "cui_prescreen_ensemble_scores"):
+                 "cui_prescreen_ensemble_scores", "cui_regions_create", "cui_regions_order"):
         getattr(lib, name).restype = C.c_int
     return lib

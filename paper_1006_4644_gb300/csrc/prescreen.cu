@@ -829,37 +829,88 @@ extern "C" cui_status cui_prescreen_ensemble_scores(const cui_prescreen *nets, i
 // Host work on O(templates) values: the bank in increasing chirp mass
 // (stable, so equal masses keep bank order), cut into `regions` equal-count
 // groups (the first n mod regions one template longer), the groups taken by
-// descending score (equal scores: lower region first).
-extern "C" cui_status cui_prescreen_rank(const double *m1, const double *m2, int64_t n_templates, const float *scores,
-                                         int32_t regions, int32_t top_k, int32_t *order_out, int64_t *n_out)
+// descending score (equal scores: lower region first).  A region plan keeps
+// the sorted bank, so that ranking one segment's scores only sorts the
+// region scores.
+struct cui_regions_s {
+    std::vector<int32_t> by_mc; // template indices in increasing chirp mass
+    int32_t regions = 0;
+    int64_t start(int64_t r) const
+    {
+        const int64_t n = (int64_t)by_mc.size(), q = n / regions, rem = n % regions;
+        return r * q + std::min<int64_t>(r, rem);
+    }
+};
+
+static cui_status regions_build(const double *m1, const double *m2, int64_t n, int32_t regions, cui_regions_s &g)
 {
-    if (!m1 || !m2 || !scores || !n_out) return ps_fail(CUI_ERR_ARG, "m1, m2, scores and n_out must be non-NULL");
-    if (n_templates < 0 || n_templates > INT32_MAX) return ps_fail(CUI_ERR_ARG, "n_templates must be in [0, 2^31)");
-    if (n_templates > 0 && !order_out) return ps_fail(CUI_ERR_ARG, "order_out must be non-NULL");
+    if (!m1 || !m2) return ps_fail(CUI_ERR_ARG, "m1 and m2 must be non-NULL");
+    if (n < 0 || n > INT32_MAX) return ps_fail(CUI_ERR_ARG, "n_templates must be in [0, 2^31)");
     if (regions < 1) return ps_fail(CUI_ERR_ARG, "regions must be >= 1");
-    if (top_k < 0) return ps_fail(CUI_ERR_ARG, "top_k must be >= 0");
-    const int64_t n = n_templates;
     std::vector<double> mc((size_t)n);
     for (int64_t i = 0; i < n; ++i) {
         if (!(m1[i] > 0.0 && m2[i] > 0.0 && std::isfinite(m1[i]) && std::isfinite(m2[i])))
             return ps_fail(CUI_ERR_ARG, "masses must be finite and > 0");
         mc[(size_t)i] = std::pow(m1[i] * m2[i], 0.6) / std::pow(m1[i] + m2[i], 0.2);
     }
-    for (int32_t r = 0; r < regions; ++r)
+    g.by_mc.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) g.by_mc[(size_t)i] = (int32_t)i;
+    std::stable_sort(g.by_mc.begin(), g.by_mc.end(),
+                     [&](int32_t a, int32_t b) { return mc[(size_t)a] < mc[(size_t)b]; });
+    g.regions = regions;
+    return CUI_OK;
+}
+
+static cui_status regions_order(const cui_regions_s &g, const float *scores, int32_t top_k, int32_t *order_out,
+                                int64_t *n_out)
+{
+    if (!scores || !n_out) return ps_fail(CUI_ERR_ARG, "scores and n_out must be non-NULL");
+    if (!g.by_mc.empty() && !order_out) return ps_fail(CUI_ERR_ARG, "order_out must be non-NULL");
+    if (top_k < 0) return ps_fail(CUI_ERR_ARG, "top_k must be >= 0");
+    for (int32_t r = 0; r < g.regions; ++r)
         if (!std::isfinite(scores[r])) return ps_fail(CUI_ERR_ARG, "scores must be finite");
-    std::vector<int32_t> by_mc((size_t)n);
-    for (int64_t i = 0; i < n; ++i) by_mc[(size_t)i] = (int32_t)i;
-    std::stable_sort(by_mc.begin(), by_mc.end(), [&](int32_t a, int32_t b) { return mc[(size_t)a] < mc[(size_t)b]; });
-    std::vector<int32_t> ranked((size_t)regions);
-    for (int32_t r = 0; r < regions; ++r) ranked[(size_t)r] = r;
+    std::vector<int32_t> ranked((size_t)g.regions);
+    for (int32_t r = 0; r < g.regions; ++r) ranked[(size_t)r] = r;
     std::stable_sort(ranked.begin(), ranked.end(), [&](int32_t a, int32_t b) { return scores[a] > scores[b]; });
-    const int64_t q = n / regions, rem = n % regions;
-    auto start = [&](int64_t r) { return r * q + std::min<int64_t>(r, rem); };
     int64_t w = 0;
-    for (int32_t k = 0; k < std::min(top_k, regions); ++k) {
+    for (int32_t k = 0; k < std::min(top_k, g.regions); ++k) {
         const int64_t r = ranked[(size_t)k];
-        for (int64_t p = start(r); p < start(r + 1); ++p) order_out[w++] = by_mc[(size_t)p];
+        for (int64_t p = g.start(r); p < g.start(r + 1); ++p) order_out[w++] = g.by_mc[(size_t)p];
     }
     *n_out = w;
     return CUI_OK;
 }
+
+extern "C" cui_status cui_prescreen_rank(const double *m1, const double *m2, int64_t n_templates, const float *scores,
+                                         int32_t regions, int32_t top_k, int32_t *order_out, int64_t *n_out)
+{
+    if (!scores || !n_out) return ps_fail(CUI_ERR_ARG, "m1, m2, scores and n_out must be non-NULL");
+    cui_regions_s g;
+    cui_status st = regions_build(m1, m2, n_templates, regions, g);
+    if (st != CUI_OK) return st;
+    return regions_order(g, scores, top_k, order_out, n_out);
+}
+
+extern "C" cui_status cui_regions_create(const double *m1, const double *m2, int64_t n_templates, int32_t regions,
+                                         cui_regions *out)
+{
+    if (!out) return ps_fail(CUI_ERR_ARG, "out must be non-NULL");
+    *out = nullptr;
+    cui_regions g = new cui_regions_s();
+    cui_status st = regions_build(m1, m2, n_templates, regions, *g);
+    if (st != CUI_OK) {
+        delete g;
+        return st;
+    }
+    *out = g;
+    return CUI_OK;
+}
+
+extern "C" cui_status cui_regions_order(cui_regions g, const float *scores, int32_t top_k, int32_t *order_out,
+                                        int64_t *n_out)
+{
+    if (!g) return ps_fail(CUI_ERR_ARG, "region plan is NULL");
+    return regions_order(*g, scores, top_k, order_out, n_out);
+}
+
+extern "C" void cui_regions_destroy(cui_regions g) { delete g; }

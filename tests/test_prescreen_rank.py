@@ -66,3 +66,20 @@ def test_errors(rank):
         rank(m, m, np.zeros(0))
     with pytest.raises(CuiError):
         rank(m, m, np.zeros(2), top_k=-1)
+
+
+def test_region_plan_matches_the_plain_formulation():
+    """cui_regions_create / cui_regions_order (the bank sorted once, reused for
+    many score vectors) give the same orders as the plain formulation."""
+    from paper_1006_4644_gb300 import Regions, build
+
+    build.build()
+    rng = np.random.default_rng(29)
+    for n, regions in [(0, 5), (7, 10), (1000, 100), (10_000, 100), (2999, 256)]:
+        m1, m2 = rng.uniform(1.0, 50.0, n), rng.uniform(1.0, 50.0, n)
+        with Regions(m1, m2, regions) as plan:
+            for _ in range(5):
+                scores = rng.normal(size=regions).astype(np.float32)
+                scores[::4] = scores[0]
+                top_k = int(rng.integers(0, regions + 3))
+                assert np.array_equal(plan.order(scores, top_k), plain_order(m1, m2, scores, top_k))
