@@ -198,6 +198,7 @@ struct cui_bank_s {
     int kx = 0;
     void *d_y = nullptr;
     Slot *d_win = nullptr;
+    Slot *d_prec = nullptr; // [batch][n1 / 2] peak records of the streamed pass 2 (tiling rpc 0)
     // plain
     void *d_h = nullptr, *d_qa = nullptr, *d_qb = nullptr;
     double *d_acc = nullptr;
@@ -311,7 +312,7 @@ static void release(cui_bank b)
                     b->d_iota, b->d_strain, b->d_psd, b->d_amp, b->d_prefix, b->d_scan, b->d_fa, b->d_fb,
                     b->tw.lo64, b->tw.hi64, b->tw.lo32, b->tw.hi32, b->tw.lodf, b->tw.hidf,
                     b->d_wbar, b->d_dS, b->d_scales, b->d_basis, b->d_basis_df, b->d_kex, b->d_gexact, b->d_y,
-                    b->d_win, b->d_h, b->d_qa, b->d_qb, b->d_acc, b->d_pwin, b->d_cluster, b->d_trig, b->d_trig_count, b->d_err,
+                    b->d_win, b->d_prec, b->d_h, b->d_qa, b->d_qb, b->d_acc, b->d_pwin, b->d_cluster, b->d_trig, b->d_trig_count, b->d_err,
                     b->d_order, b->d_psd_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -383,8 +384,10 @@ static cudaError_t configure_fused(cui_bank b, const cui_tuning &tu)
     }
     if (b->d_y) cudaFree(b->d_y);
     if (b->d_win) cudaFree(b->d_win);
+    if (b->d_prec) cudaFree(b->d_prec);
     b->d_y = nullptr;
     b->d_win = nullptr;
+    b->d_prec = nullptr;
     b->n1 = tu.n1;
     b->n2 = (int)(b->n / tu.n1);
     b->ccols = tu.ccols;
@@ -394,6 +397,7 @@ static cudaError_t configure_fused(cui_bank b, const cui_tuning &tu)
     b->ny = b->nt > b->batch ? 2 : 1;
     if ((e = cudaMalloc(&b->d_y, per * (size_t)b->batch * b->ny)) != cudaSuccess) return e;
     if ((e = dalloc(&b->d_win, (int64_t)b->batch * std::max(1, b->nwin))) != cudaSuccess) return e;
+    if (tu.rpc == 0 && (e = dalloc(&b->d_prec, (int64_t)b->batch * (tu.n1 / 2))) != cudaSuccess) return e;
     e = cudaMemsetAsync(b->d_win, 0, sizeof(Slot) * (size_t)b->batch * std::max(1, b->nwin), s);
     if (e != cudaSuccess) return e;
     return build_phase_tables(b, tu.n1, tu.ccols);
@@ -627,6 +631,8 @@ static FusedArgs fused_args(cui_bank b, const int32_t *order, int64_t base)
     a.base = base;
     a.ywork = b->d_y;
     a.peak = b->d_peak;
+    a.prec = b->d_prec;
+    a.nrec = b->n1 / 2;
     a.win = b->d_win;
     a.err = b->d_err;
     a.cas_rounds = b->cas_rounds;
@@ -661,6 +667,8 @@ static FinalizeArgs finalize_args(cui_bank b, const int32_t *d_ord, cui_peak *po
     FinalizeArgs fa;
     fa.order = d_ord;
     fa.peak = b->d_peak;
+    fa.prec = b->fused && b->rpc == 0 ? b->d_prec : nullptr; // the streamed pass 2 writes records
+    fa.nrec = b->n1 / 2;
     fa.win = b->d_win;
     fa.nwin = b->nwin;
     fa.lo = b->desc.valid_lo;

@@ -378,6 +378,33 @@ __device__ __forceinline__ void slot_max(Slot *s, unsigned long long key, float 
     atomicOr(err, 2);
 }
 
+// slot_max on a slot in shared memory (the same bounded loop, 128-bit CAS in
+// the shared state space): for a CTA that reduces its own maximum before one
+// plain store of the slot to global memory.
+__device__ __forceinline__ void slot_max_shared(Slot *s, unsigned long long key, float phase, int *err, int rounds)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(s);
+    unsigned long long cur_lo = *(volatile unsigned long long *)&s->key;
+    unsigned long long cur_hi = *(volatile unsigned long long *)&s->phase_bits;
+    const unsigned long long new_hi = (unsigned long long)__float_as_uint(phase);
+    for (int it = 0; it < rounds; ++it) {
+        if (cur_lo >= key) return;
+        unsigned long long old_lo, old_hi;
+        asm volatile("{\n\t.reg .b128 d, c, n;\n\t"
+                     "mov.b128 c, {%2, %3};\n\t"
+                     "mov.b128 n, {%4, %5};\n\t"
+                     "atom.shared.cas.b128 d, [%6], c, n;\n\t"
+                     "mov.b128 {%0, %1}, d;\n\t}"
+                     : "=l"(old_lo), "=l"(old_hi)
+                     : "l"(cur_lo), "l"(cur_hi), "l"(key), "l"(new_hi), "r"(a)
+                     : "memory");
+        if (old_lo == cur_lo && old_hi == cur_hi) return;
+        cur_lo = old_lo;
+        cur_hi = old_hi;
+    }
+    atomicOr(err, 2);
+}
+
 // Bank-wide window slot: raise it to (key, template, phase) if (key, lower
 // template) is larger; the template is kept as 0xFFFFFFFF - tmpl in `pad`, so
 // among equal keys the lowest template wins.  Same bounded CAS as slot_max.

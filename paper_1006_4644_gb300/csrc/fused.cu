@@ -496,10 +496,12 @@ __device__ __forceinline__ int64_t p2_find(const E *v, int lt, float M, const in
 // c_l = c + l n1/2; |z|^2 is compared before the (positive) scaling.  The
 // maximum of |z|^2 over the NW warps that share `s_max` is reduced first
 // (`bar` is their barrier); only the threads that hold it then look for their
-// lowest sample with it and raise the peak slot of template t.
+// lowest sample with it and raise a peak slot: the template's global slot, or
+// with a shared `local` slot that one (so that no thread waits on an L2 round
+// trip here; the caller stores it to global memory later).
 template <int L, int RL, int PPT, int NW, typename E, typename Bar>
 __device__ __forceinline__ void p2_epilogue(const E *v, int lg, int c, int y, int t, const FusedArgs &p, float *s_max,
-                                            Bar bar)
+                                            Bar bar, Slot *local = nullptr)
 {
     constexpr int NL = lanes_of<E>;
     constexpr int TPR = L / PPT;
@@ -559,7 +561,8 @@ __device__ __forceinline__ void p2_epilogue(const E *v, int lg, int c, int y, in
     if (M >= 0.f && mx == M) {
         float2 zb = make_float2(0.f, 0.f);
         const int64_t sb = p2_find<L, RL, PPT>(v, lg, M, cl, n1, dlo, dhi, zb);
-        slot_max(p.peak + t, make_key(M * inv, (uint32_t)sb), atan2f(zb.y, zb.x), p.err, p.cas_rounds);
+        if (local) slot_max_shared(local, make_key(M * inv, (uint32_t)sb), atan2f(zb.y, zb.x), p.err, p.cas_rounds);
+        else slot_max(p.peak + t, make_key(M * inv, (uint32_t)sb), atan2f(zb.y, zb.x), p.err, p.cas_rounds);
     }
 }
 
@@ -786,6 +789,7 @@ template <typename ST> __global__ void __launch_bounds__(2 * kStreamTeam, 1) k_p
     __shared__ float s_max[2][NW];
     __shared__ __align__(8) uint64_t full[2];
     __shared__ int abort_flag[2], issued[2], consumed[2];
+    __shared__ Slot s_peak[2]; // each team's peak of its current row pair
     const int tid = threadIdx.x;
     const int team = tid / TPR, lt = tid % TPR;
     // last two stages on half-warp groups (as in k_pass2 for 4096-point rows)
@@ -804,6 +808,7 @@ template <typename ST> __global__ void __launch_bounds__(2 * kStreamTeam, 1) k_p
         abort_flag[0] = abort_flag[1] = 0;
         issued[0] = issued[1] = 0;
         consumed[0] = consumed[1] = 0;
+        s_peak[0] = s_peak[1] = Slot{0ull, 0u, 0u};
     }
     __syncthreads();
     if (tid == 0 && (int)blockIdx.x < total) {
@@ -813,7 +818,8 @@ template <typename ST> __global__ void __launch_bounds__(2 * kStreamTeam, 1) k_p
     // root of the last stage's twiddles: the same for every row pair
     const float2 wl = p2_root<R>(lg, L / R);
 
-    int j = 0; // row pairs this team has taken
+    int j = 0;     // row pairs this team has taken
+    int prev = -1; // the team's previous row pair, whose peak record is still in s_peak
     for (int i = blockIdx.x + team * G; i < total; i += 2 * G, ++j) {
         if (!mbar_wait(&full[team], j & 1, p.copy_wait_ns)) {
             abort_flag[team] = 1;
@@ -837,6 +843,11 @@ template <typename ST> __global__ void __launch_bounds__(2 * kStreamTeam, 1) k_p
         p2_store<L, R, 1, PPT>(v, row, lt);
         named_sync(bar_team, TPR);
         if (abort_flag[team]) break; // the same in every thread of the team after the barrier
+        if (lt == 0 && prev >= 0) { // the previous row pair's peak (its CAS came before this barrier)
+            p.prec[prev] = s_peak[team];
+            s_peak[team] = Slot{0ull, 0u, 0u};
+        }
+        prev = i;
         const int y = i / npairs, c = i % npairs;
         {
             // Y is read exactly once: drop its L2 lines so that they are never written back
@@ -850,10 +861,12 @@ template <typename ST> __global__ void __launch_bounds__(2 * kStreamTeam, 1) k_p
         __syncwarp();
         p2_stage<L, R, L / R, false, PPT>(v, row, lg, tw1, &wl);
         const int t = p.order[p.base + y];
-        p2_epilogue<L, R, PPT, NW>(v, lg, c, y, t, p, s_max[team], [bar_team] { named_sync(bar_team, TPR); });
+        p2_epilogue<L, R, PPT, NW>(v, lg, c, y, t, p, s_max[team], [bar_team] { named_sync(bar_team, TPR); },
+                                   &s_peak[team]);
     }
     if (lt == 0) consumed[team] = j;
     __syncthreads();
+    if (lt == 0 && prev >= 0) p.prec[prev] = s_peak[team]; // the team's last row pair
     // a team that gave up can leave one copy in flight: let it land first
     if (tid == 0)
         for (int q = 0; q < 2; ++q)
@@ -1297,6 +1310,51 @@ __device__ __forceinline__ void decode(const Slot &sl, int64_t &sample, float &s
     phase = __uint_as_float(sl.phase_bits);
 }
 
+// The largest record of template y (key order: rho^2, then the lower sample);
+// one warp per template.
+__device__ __forceinline__ Slot best_record(const Slot *rec, int nrec)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long key = 0ull;
+    unsigned int ph = 0u;
+    for (int r = lane; r < nrec; r += 32) {
+        const Slot q = rec[r];
+        if (q.key > key) {
+            key = q.key;
+            ph = q.phase_bits;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, off);
+        const unsigned int p2 = __shfl_xor_sync(0xffffffffu, ph, off);
+        if (k2 > key) {
+            key = k2;
+            ph = p2;
+        }
+    }
+    return Slot{key, ph, 0u};
+}
+
+__global__ void k_finalize_records(const FinalizeArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    for (int y = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; y < a.count; y += (gridDim.x * blockDim.x) >> 5) {
+        const Slot sl = best_record(a.prec + (size_t)y * a.nrec, a.nrec);
+        if (lane != 0) continue;
+        const int t = a.order[a.base + y];
+        cui_peak o;
+        if (sl.key == 0ull) {
+            o.sample = a.lo;
+            o.snr = 0.f;
+            o.phase = 0.f;
+        } else {
+            decode(sl, o.sample, o.snr, o.phase);
+        }
+        a.peaks_out[t] = o;
+    }
+}
+
 __global__ void k_finalize_peaks(const FinalizeArgs a)
 {
     for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < a.count; y += gridDim.x * blockDim.x) {
@@ -1337,8 +1395,13 @@ __global__ void k_finalize_windows(const FinalizeArgs a)
 
 cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s)
 {
-    const int pb = (a.count + 255) / 256;
-    k_finalize_peaks<<<pb < 1216 ? pb : 1216, 256, 0, s>>>(a);
+    if (a.prec) {
+        const int wb = (a.count + 7) / 8; // 8 warps per CTA, one per template
+        k_finalize_records<<<wb < 1216 ? wb : 1216, 256, 0, s>>>(a);
+    } else {
+        const int pb = (a.count + 255) / 256;
+        k_finalize_peaks<<<pb < 1216 ? pb : 1216, 256, 0, s>>>(a);
+    }
     const int64_t total = (int64_t)a.count * a.nwin;
     const int64_t wb = (total + 255) / 256;
     k_finalize_windows<<<(unsigned)(wb < 4864 ? (wb > 0 ? wb : 1) : 4864), 256, 0, s>>>(a);

@@ -87,6 +87,8 @@ struct FusedArgs {
     int64_t base;           // first position of this batch in `order`
     void *ywork;            // [B][N] spectrum between the two passes
     Slot *peak;             // [T] peak slots
+    Slot *prec;             // [B][nrec] per-row-pair peak records of the streamed pass 2 (else unused)
+    int nrec;               // records per template (row pairs, n1 / 2)
     Slot *win;              // [B][nwin] window slots
     int *err;               // device error word
     int cas_rounds;         // bound of the compare-and-swap loops (kCasRounds)
@@ -125,6 +127,8 @@ struct FinalizeArgs {
     int64_t base;            // first position in `order`
     int count;               // templates in this batch
     Slot *peak;              // [T]
+    const Slot *prec;        // [count][nrec] peak records (streamed pass 2), or NULL: the peak slots hold the peaks
+    int nrec;
     Slot *win;               // [count][nwin]
     int nwin;
     int64_t lo, window;

@@ -59,6 +59,9 @@ def main():
     ap.add_argument("--ensemble", type=int, default=3,
                     help="networks trained from seeds seed, seed+1, ...; regions ranked by their mean probability")
     ap.add_argument("--labels", default="region", choices=["region", "response"])
+    ap.add_argument("--response-cache", default=None,
+                    help="npz of the training segments' responding regions (bit masks): read when present, "
+                         "else written after the exhaustive bank has computed them")
     args = ap.parse_args()
 
     import multiprocessing as mp
@@ -110,19 +113,24 @@ def main():
             """Mean over the networks of the region probabilities (in the library)."""
             ensemble_scores(nets, x, out)
 
-        def feats(start, count, keep_meta=False, label_bank=None, responses=None):
+        def feats(start, count, keep_meta=False, label_bank=None, responses=None, masks=None):
             X, Y, M, D = [], [], [], []
             for s0 in range(start, start + count, 2048):
                 d, y, meta = make_segments_mp(4, s0, min(2048, start + count - s0), n, fs, f_low, psd, bounds, R,
                                               pool=pool)
                 out = torch.zeros((len(d), p.bands, p.frames), dtype=torch.float32, device="cuda")
                 p.features(torch.from_numpy(d).cuda(), psd_d, out)
-                if label_bank is not None:
+                if label_bank is not None or masks is not None:
                     for i in range(len(d)):
-                        reg = region_response(label_bank, d[i], meta[i]["j0"])
-                        if responses is not None and len(responses) < 512:
-                            responses.append(reg)
-                        hit = reg >= 8.0
+                        g = s0 - start + i
+                        if label_bank is not None:
+                            reg = region_response(label_bank, d[i], meta[i]["j0"])
+                            if responses is not None and len(responses) < 512:
+                                responses.append(reg)
+                            hit = reg >= 8.0
+                            new_masks.append(np.packbits(hit))
+                        else:
+                            hit = np.unpackbits(masks[g])[:R].astype(bool)
                         if hit.any():
                             y[i] = hit / hit.sum()
                             hits.append(int(hit.sum()))
@@ -135,10 +143,21 @@ def main():
 
         t0 = time.perf_counter()
         hits = []  # regions responding at rho >= 8, per training segment that has any
-        if args.labels == "response":
+        new_masks = []
+        if args.labels == "response" and args.response_cache and os.path.exists(args.response_cache):
+            cached = np.load(args.response_cache)["masks"]
+            if len(cached) < args.train:
+                raise ValueError("the response cache holds fewer segments than --train")
+            xtr, ytr, _, _ = feats(0, args.train, masks=cached)
+            rep["labels_response"] = {"segments_with_a_response": len(hits),
+                                      "mean_regions_responding": float(np.mean(hits)) if hits else 0.0,
+                                      "from_cache": True}
+        elif args.labels == "response":
             responses = []
             with Bank(m1, m2, n=n, fs=fs, f_low=f_low, pn_x2=7, snr_threshold=6.0, window=W) as lb:
                 xtr, ytr, _, _ = feats(0, args.train, label_bank=lb, responses=responses)
+            if args.response_cache:
+                np.savez_compressed(args.response_cache, masks=np.stack(new_masks))
             rep["labels_response"] = {"segments_with_a_response": len(hits),
                                       "mean_regions_responding": float(np.mean(hits)) if hits else 0.0}
             path = os.path.join(ROOT, "tests", "prescreen_labels", "oracle_response_seed4.npz")
@@ -232,8 +251,9 @@ def main():
                 p.bank_features(bank, feat1)
                 score(feat1, sc1)
                 ev[2].record(stream)
+                sc_host = sc1.cpu().numpy()[0]  # waits for the scores
                 h0 = time.perf_counter()
-                order = plan.order(sc1.cpu().numpy()[0], k_star)
+                order = plan.order(sc_host, k_star)
                 h1 = time.perf_counter()
                 ev[3].record(stream)
                 bank.filter(order)
@@ -248,7 +268,7 @@ def main():
                 t_host += 1e3 * (h1 - h0)
             rep["exhaustive_ms"] = t_ex / reps
             rep["prescreen_plus_topK_ms"] = t_ps / reps
-            rep["prescreen_breakdown_ms"] = {"features_and_scores": t_feat / reps, "read_and_rank_host": t_host / reps,
+            rep["prescreen_breakdown_ms"] = {"features_and_scores": t_feat / reps, "rank_host": t_host / reps,
                                              "top_k_filter": t_top / reps}
             rep["speedup"] = t_ex / t_ps
             # the same timing at the 99 % and 95 % points (misses allowed)
