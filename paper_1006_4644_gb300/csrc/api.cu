@@ -397,7 +397,9 @@ static cudaError_t configure_fused(cui_bank b, const cui_tuning &tu)
     b->ny = b->nt > b->batch ? 2 : 1;
     if ((e = cudaMalloc(&b->d_y, per * (size_t)b->batch * b->ny)) != cudaSuccess) return e;
     if ((e = dalloc(&b->d_win, (int64_t)b->batch * std::max(1, b->nwin))) != cudaSuccess) return e;
-    if (tu.rpc == 0 && (e = dalloc(&b->d_prec, (int64_t)b->batch * (tu.n1 / 2))) != cudaSuccess) return e;
+    if (tu.rpc == 0 &&
+        (e = dalloc(&b->d_prec, (int64_t)b->batch * fused_records_per_template(tu.n1, b->n2))) != cudaSuccess)
+        return e;
     e = cudaMemsetAsync(b->d_win, 0, sizeof(Slot) * (size_t)b->batch * std::max(1, b->nwin), s);
     if (e != cudaSuccess) return e;
     return build_phase_tables(b, tu.n1, tu.ccols);
@@ -632,7 +634,7 @@ static FusedArgs fused_args(cui_bank b, const int32_t *order, int64_t base)
     a.ywork = b->d_y;
     a.peak = b->d_peak;
     a.prec = b->d_prec;
-    a.nrec = b->n1 / 2;
+    a.nrec = b->n1 > 0 ? fused_records_per_template(b->n1, b->n2) : 0;
     a.win = b->d_win;
     a.err = b->d_err;
     a.cas_rounds = b->cas_rounds;
@@ -668,7 +670,7 @@ static FinalizeArgs finalize_args(cui_bank b, const int32_t *d_ord, cui_peak *po
     fa.order = d_ord;
     fa.peak = b->d_peak;
     fa.prec = b->fused && b->rpc == 0 ? b->d_prec : nullptr; // the streamed pass 2 writes records
-    fa.nrec = b->n1 / 2;
+    fa.nrec = b->n1 > 0 ? fused_records_per_template(b->n1, b->n2) : 0;
     fa.win = b->d_win;
     fa.nwin = b->nwin;
     fa.lo = b->desc.valid_lo;

@@ -873,6 +873,151 @@ template <typename ST> __global__ void __launch_bounds__(2 * kStreamTeam, 1) k_p
             if (issued[q] > consumed[q] && !mbar_wait(&full[q], consumed[q] & 1, kCopyWaitNs)) atomicOr(p.err, 4);
 }
 
+// Streamed pass 2 for unpaired rows of 16384 points (N = 2^22 with n1 = 256).
+// A row (128 KiB in complex64) and its padded exchange buffer leave no room
+// for a second row, so the next row arrives in two halves: the first half into
+// a staging buffer S as soon as the current row's stage-0 inputs have been
+// read (it lands during stages 1-3), the second half into the first bytes of
+// the exchange buffer once the last stage has read it (it lands during the
+// last transform and the epilogue).  One persistent CTA of 1024 threads per
+// SM; the row's transform is that of k_pass2 (radices 4, 16, 16, 16, the last
+// two on half-warp groups), so the results are bit-identical.  Waits and the
+// error path as in k_pass2_stream.
+constexpr int kStream16L = 16384;
+constexpr int kStream16Threads = 1024;
+
+template <typename ST> constexpr size_t s16_half_bytes() { return (size_t)(kStream16L / 2) * sizeof(ST); }
+template <typename ST> constexpr size_t s16_smem()
+{
+    return s16_half_bytes<ST>() + (size_t)padded<kStream16L>() * sizeof(float2);
+}
+
+template <typename ST> __device__ __forceinline__ float2 elem_from(ST q);
+template <> __device__ __forceinline__ float2 elem_from<float2>(float2 q) { return q; }
+template <> __device__ __forceinline__ float2 elem_from<__nv_bfloat162>(__nv_bfloat162 q) { return __bfloat1622float2(q); }
+
+// Copy half `h` (0 or 1) of row `item` (ROWB = 2 HALF bytes at ywork + item ROWB)
+// into dst, completing its bytes on *bar.  One thread.
+template <typename ST>
+__device__ __forceinline__ void s16_issue_half(const FusedArgs &p, int item, int h, void *dst, uint64_t *bar)
+{
+    constexpr unsigned HALF = (unsigned)s16_half_bytes<ST>();
+    const char *src = (const char *)p.ywork + (size_t)item * 2 * HALF + (size_t)h * HALF;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 2; ++q) bulk_load((char *)dst + q * (HALF / 2), src + q * (HALF / 2), HALF / 2, bar);
+}
+
+// Grid min(SMs, rows of the batch), 1024 threads; row i of the batch is
+// template y = i / n1, row c = i mod n1.
+template <typename ST> __global__ void __launch_bounds__(kStream16Threads, 1) k_pass2_stream16k(const FusedArgs p, int count)
+{
+    constexpr int L = kStream16L, PPT = 16, TPR = kStream16Threads, NW = TPR / 32;
+    constexpr int R0 = 4, R1 = 16, R2 = 16, RL = 16, NSL = L / RL;
+    constexpr int T0 = PPT / R0;
+    constexpr unsigned HALF = (unsigned)s16_half_bytes<ST>();
+    extern __shared__ __align__(128) float4 sm4[];
+    const ST *S = reinterpret_cast<const ST *>(sm4);
+    float2 *row = reinterpret_cast<float2 *>((char *)sm4 + HALF);
+    const ST *Wraw = reinterpret_cast<const ST *>(row); // the second half of the next row, before stage 0 pads it
+    __shared__ float2 tw1[R0 * R1];
+    __shared__ float2 tw2[R0 * R1 * R2];
+    __shared__ float s_max[NW];
+    __shared__ __align__(8) uint64_t full;
+    __shared__ int abort_flag, issued;
+    __shared__ Slot s_peak;
+    const int tid = threadIdx.x;
+    const int lt = tid;
+    const int lg = (lt & 15) * (L / 256) + (lt >> 4); // the last two stages on half-warp groups
+    const int n1 = p.n1;
+    const int total = count * n1; // <= 64 templates x 256 rows in practice (4 GiB of Y at most)
+    const int G = gridDim.x;
+
+    for (int m = tid; m < R0 * R1; m += TPR) tw1[m] = turn((m % R0) * (m / R0), R0 * R1);
+    for (int m = tid; m < R0 * R1 * R2; m += TPR) tw2[m] = turn((m % (R0 * R1)) * (m / (R0 * R1)), R0 * R1 * R2);
+    if (tid == 0) {
+        mbar_init(&full, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+        issued = 0;
+        s_peak = Slot{0ull, 0u, 0u};
+    }
+    __syncthreads();
+    if (tid == 0 && (int)blockIdx.x < total) {
+        issued = 1;
+        mbar_expect_tx(&full, 2 * HALF);
+        s16_issue_half<ST>(p, blockIdx.x, 0, (void *)S, &full);
+        s16_issue_half<ST>(p, blockIdx.x, 1, (void *)row, &full);
+    }
+    const float2 wl = p2_root<RL>(lg, NSL);
+
+    int j = 0, prev = -1;
+    for (int i = blockIdx.x; i < total; i += G, ++j) {
+        if (!mbar_wait(&full, j & 1, p.copy_wait_ns)) {
+            abort_flag = 1;
+            atomicOr(p.err, 4);
+        }
+        float2 v[PPT];
+#pragma unroll
+        for (int t = 0; t < T0; ++t)
+#pragma unroll
+            for (int r = 0; r < R0; ++r) {
+                const int x = lt + t * TPR + r * (L / R0); // quarter r of the row
+                v[t * R0 + r] = elem_from<ST>(r < 2 ? S[x] : Wraw[x - L / 2]);
+            }
+#pragma unroll
+        for (int t = 0; t < T0; ++t) dft<R0, +1>(v + t * R0);
+        __syncthreads(); // every thread has read S and the raw half; abort_flag settled
+        if (abort_flag) break;
+        const bool has_next = i + G < total;
+        if (tid == 0) {
+            if (prev >= 0) { // the previous row's peak (its CAS came before this barrier)
+                p.prec[prev] = s_peak;
+                s_peak = Slot{0ull, 0u, 0u};
+            }
+            if (has_next) { // the next row's first half lands while this row is transformed
+                issued += 1;
+                mbar_expect_tx(&full, 2 * HALF);
+                s16_issue_half<ST>(p, i + G, 0, (void *)S, &full);
+            }
+        }
+        prev = i;
+        p2_store<L, R0, 1, PPT>(v, row, lt);
+        __syncthreads();
+        {
+            const char *yb = (const char *)p.ywork + (size_t)i * 2 * HALF;
+            for (int m = tid; m < (int)(2 * HALF / 128); m += TPR)
+                asm volatile("discard.global.L2 [%0], 128;" ::"l"(yb + (size_t)m * 128) : "memory");
+        }
+        p2_stage<L, R1, R0, true, PPT>(v, row, lt, tw1);
+        __syncthreads();
+        p2_store<L, R1, R0, PPT>(v, row, lt);
+        __syncthreads();
+        p2_stage<L, R2, R0 * R1, true, PPT>(v, row, lg, tw2);
+        __syncwarp();
+        p2_store<L, R2, R0 * R1, PPT>(v, row, lg);
+        __syncwarp();
+        p2_stage<L, RL, NSL, false, PPT>(v, row, lg, tw1, &wl);
+        const int y = i / n1, c = i % n1;
+        const int t = p.order[p.base + y];
+        // the epilogue's barrier comes after every thread's last read of the
+        // exchange buffer: then the next row's second half may land in it
+        p2_epilogue<L, RL, PPT, NW>(
+            v, lg, c, y, t, p, s_max,
+            [&] {
+                __syncthreads();
+                if (tid == 0 && has_next) s16_issue_half<ST>(p, i + G, 1, (void *)row, &full);
+            },
+            &s_peak);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (prev >= 0) p.prec[prev] = s_peak; // the last row's peak
+        // a wait that gave up leaves that row's copies in flight: let them land first
+        if (issued > j && !mbar_wait(&full, j & 1, kCopyWaitNs)) atomicOr(p.err, 4);
+    }
+}
+
 // ------------------------------------------------------------ dispatch ----
 // Opt the kernel in to `bytes` of dynamic shared memory.  Always set: the
 // 48 KB default covers static plus dynamic memory, so a dynamic size below
@@ -888,9 +1033,11 @@ constexpr int kPairMaxL = 8192;   // pass 2 runs on row pairs up to this row len
 static bool paired(int n2) { return n2 <= kPairMaxL; }
 
 size_t fused_pass1_smem(int n1, int ccols) { return (size_t)n1 * ccols * sizeof(float2); }
+int fused_records_per_template(int n1, int n2) { return n2 <= kPairMaxL ? n1 / 2 : n1; }
+
 size_t fused_pass2_smem(int n2, int rpc)
 {
-    if (rpc == 0) return stream_smem<float2>();
+    if (rpc == 0) return n2 == kStream16L ? s16_smem<float2>() : stream_smem<float2>();
     int lp = n2 + n2 / 16; // padded<L>() of the kernel
     if (n2 == 4096) lp = padded<4096>();
     if (n2 == 16384) lp = padded<16384>();
@@ -906,8 +1053,8 @@ bool fused_tiling_ok(int log2n, int n1, int ccols, int rpc)
     const int64_t n2 = (int64_t(1) << log2n) / n1;
     if (n2 % ccols) return false;
     // rpc 0: the streamed persistent pass 2 (k_pass2_stream)
-    static const int pass2[][2] = {{64, 32},  {128, 16}, {256, 8},  {512, 4},  {1024, 4},         {2048, 2},
-                                   {4096, 2}, {4096, 1}, {4096, 0}, {8192, 1}, {16384, 1}};
+    static const int pass2[][2] = {{64, 32},  {128, 16}, {256, 8},  {512, 4},  {1024, 4},  {2048, 2},
+                                   {4096, 2}, {4096, 1}, {4096, 0}, {8192, 1}, {16384, 1}, {16384, 0}};
     for (auto &q : pass2)
         if (q[0] == n2 && q[1] == rpc) return true;
     return false;
@@ -917,7 +1064,7 @@ void fused_default_tiling(int log2n, int *n1, int *ccols, int *rpc)
 {
     static const int tab[23][2] = {{0, 0},  {0, 0},  {0, 0},  {0, 0},  {0, 0},  {0, 0},  {0, 0},  {0, 0},
                                    {0, 0},  {0, 0},  {0, 0},  {0, 0},  {64, 32}, {64, 16}, {64, 8}, {64, 4},
-                                   {64, 4}, {128, 4}, {256, 4}, {256, 2}, {256, 0}, {256, 1}, {256, 1}};
+                                   {64, 4}, {128, 4}, {256, 4}, {256, 2}, {256, 0}, {256, 1}, {256, 0}};
     *n1 = tab[log2n][0];
     *rpc = tab[log2n][1];
     // N = 2^20: the tiling the autotuner picks on GB300 (streamed pass 2, 16 columns per pass-1 CTA)
@@ -989,10 +1136,25 @@ template <typename ST> static cudaError_t run_pass2_stream(const FusedArgs &a, i
     return cudaGetLastError();
 }
 
+template <typename ST> static cudaError_t run_pass2_stream16k(const FusedArgs &a, int count, cudaStream_t s)
+{
+    auto k = k_pass2_stream16k<ST>;
+    const size_t smem = s16_smem<ST>();
+    cudaError_t e = allow_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)count * a.n1;
+    const int sms = sm_count();
+    if (sms <= 0) return cudaErrorInvalidDevice;
+    if (total <= 0) return cudaSuccess;
+    k<<<(unsigned)std::min<int64_t>(sms, total), kStream16Threads, smem, s>>>(a, count);
+    return cudaGetLastError();
+}
+
 template <typename ST> static cudaError_t pass2_dispatch(const FusedArgs &a, int count, cudaStream_t s)
 {
     const int L = a.n2, R = a.rpc;
     if (L == kStreamL && R == 0) return run_pass2_stream<ST>(a, count, s);
+    if (L == kStream16L && R == 0) return run_pass2_stream16k<ST>(a, count, s);
     if (L == 64 && R == 32) return run_pass2<64, 32, ST, 4, 16, 1, 1>(a, count, s);
     if (L == 128 && R == 16) return run_pass2<128, 16, ST, 8, 16, 1, 1>(a, count, s);
     if (L == 256 && R == 8) return run_pass2<256, 8, ST, 16, 16, 1, 1>(a, count, s);

@@ -88,7 +88,7 @@ struct FusedArgs {
     void *ywork;            // [B][N] spectrum between the two passes
     Slot *peak;             // [T] peak slots
     Slot *prec;             // [B][nrec] per-row-pair peak records of the streamed pass 2 (else unused)
-    int nrec;               // records per template (row pairs, n1 / 2)
+    int nrec;               // records per template (fused_records_per_template)
     Slot *win;              // [B][nwin] window slots
     int *err;               // device error word
     int cas_rounds;         // bound of the compare-and-swap loops (kCasRounds)
@@ -108,6 +108,8 @@ bool fused_tiling_ok(int log2n, int n1, int ccols, int rpc);
 void fused_default_tiling(int log2n, int *n1, int *ccols, int *rpc);
 size_t fused_pass1_smem(int n1, int ccols);
 size_t fused_pass2_smem(int n2, int rpc);
+// peak records per template of the streamed pass 2 (rpc 0): its row pairs, or its rows when unpaired
+int fused_records_per_template(int n1, int n2);
 cudaError_t launch_pass1(const FusedArgs &a, int count, cudaStream_t s);
 cudaError_t launch_pass2(const FusedArgs &a, int count, cudaStream_t s);
 constexpr int kChisqMaxBands = 64;

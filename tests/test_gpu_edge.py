@@ -131,7 +131,8 @@ def test_error_statuses(seg):
         _bank(m=(np.array([1.0, -1.0]), np.array([1.0, 1.0])))
 
 
-@pytest.mark.parametrize("case", ["fused_rounds0", "fused_rounds1_contended", "plain_rounds0", "streamed_wait0"])
+@pytest.mark.parametrize("case", ["fused_rounds0", "fused_rounds1_contended", "plain_rounds0", "streamed_wait0",
+                                  "streamed16k_wait0"])
 def test_bounded_waits_report_a_timeout_and_the_handle_recovers(case):
     """The device waits are bounded and a wait that runs out is reported, not
     hung on.  cui_bank_set_wait_bounds lowers the bounds: no round of the
@@ -147,6 +148,9 @@ def test_bounded_waits_report_a_timeout_and_the_handle_recovers(case):
     if case == "streamed_wait0":
         w = synth.Workload("edge18", 1 << 18, 4096.0, 30.0, 7, 4, 1.0, 6.0, False, 1, 25.0, 25.0, 1.0, 4343)
         strain, psd, dt, _ = make_segment(w)
+    elif case == "streamed16k_wait0":
+        w = synth.Workload("edge22", 1 << 22, 4096.0, 30.0, 7, 2, 1.0, 6.0, False, 1, 25.0, 25.0, 1.0, 4344)
+        strain, psd, dt, _ = make_segment(w)
     else:
         w = W
         strain, psd, dt, _ = make_segment(W)
@@ -156,8 +160,10 @@ def test_bounded_waits_report_a_timeout_and_the_handle_recovers(case):
                ) as b:
         if case == "streamed_wait0":
             b.set_tuning(64, 16, 0, w.n_templates)
+        elif case == "streamed16k_wait0":
+            b.set_tuning(256, 32, 0, w.n_templates)
         b.upload(strain, psd)
-        if case == "streamed_wait0":
+        if case.startswith("streamed"):
             b.set_wait_bounds(-1, 0)
         else:
             b.set_wait_bounds(1 if "rounds1" in case else 0, -1)

@@ -102,15 +102,18 @@ def test_autotune_selects_a_valid_tiling():
 
 
 @pytest.mark.parametrize("log2n,n1,count,batch", [(18, 64, 5, 5), (19, 128, 3, 2), (20, 256, 1, 1),
-                                                  (20, 256, 3, 3), (20, 256, 7, 4)])
+                                                  (20, 256, 3, 3), (20, 256, 7, 4), (22, 256, 1, 1),
+                                                  (22, 256, 3, 2)])
 def test_streamed_pass2_equals_row_pair_kernel(log2n, n1, count, batch):
-    """The streamed persistent pass 2 (rpc 0: row pairs copied into shared
-    memory by the bulk-copy engine, two teams per CTA) runs the same arithmetic
-    in the same order as the one-row-pair-per-CTA kernel, so peaks and
-    triggers are bit-identical.  The cases cover fewer row pairs than SMs (one
-    template at 2^20: 128 row pairs, the second team idle), both teams, ragged
-    last batches, and a valid range that cuts rows; the error word must stay
-    clear (a bounded bulk-copy wait that gave up would read CUI_ERR_TIMEOUT)."""
+    """The streamed persistent pass 2 (rpc 0: rows copied into shared memory
+    by the bulk-copy engine; row pairs of 4096 points on two teams per CTA, or
+    unpaired 16384-point rows arriving in two halves) runs the same arithmetic
+    in the same order as the one-row-per-CTA kernels, so peaks and triggers are
+    bit-identical.  The cases cover fewer row pairs than SMs (one template at
+    2^20: 128 row pairs, the second team idle), both teams, CTAs with one and
+    with two rows at 2^22, ragged last batches, and a valid range that cuts
+    rows; the error word must stay clear (a bounded bulk-copy wait that gave up
+    would read CUI_ERR_TIMEOUT)."""
     from paper_1006_4644_gb300 import Bank
 
     n = 1 << log2n
@@ -124,7 +127,7 @@ def test_streamed_pass2_equals_row_pair_kernel(log2n, n1, count, batch):
         with Bank(m1, m2, n=n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, snr_threshold=4.5, window=1000,
                   valid=(lo, hi)) as b:
             b.upload(strain, psd)
-            b.set_tuning(n1, 16, rpc, batch)
+            b.set_tuning(n1, 32 if log2n == 22 else 16, rpc, batch)
             b.filter()
             b.filter()  # a second call over the same buffers
             out[rpc] = (b.peaks(), b.triggers()[0])
