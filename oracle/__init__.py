@@ -31,9 +31,10 @@ Each function names the part of the paper it follows:
   segments, and the data restricted to a band and resampled)
 * ``fft`` / ``dft``    -- textbook radix-2 FFT and naive DFT used above
 
-Parity unpinned: the absolute constant of Psi (-pi/4 and the constant part of
-the 2.5PN logarithm) is a convention; it moves every reported phase by the
-same constant and changes no rho.
+The absolute constant of Psi (the -pi/4 of the stationary phase and the
+constant part of the 2.5PN logarithm, referred to v_lso) is pinned by a direct
+Fourier transform of the time-domain chirp of ``oracle.td``: zero offset below
+2.5PN, 9 alpha_5 ln 6 / (256 eta) at 2.5PN (tests/test_oracle_phase_constant.py).
 """
 
 from __future__ import annotations
