@@ -212,6 +212,15 @@ def main():
         rng = np.random.default_rng(0)
         k_net, k_rand, detectable = [], [], 0
         k_single = [[] for _ in nets]
+        # ranking by the region probability summed over +-w neighbouring regions: the
+        # chance that a region's templates respond, when responses span neighbours
+        widths = (1, 2, 4, 8)
+        k_smooth = {w: [] for w in widths}
+
+        def smooth(pr, w):
+            c = np.concatenate([[0.0], np.cumsum(pr)])
+            idx = np.arange(R)
+            return c[np.minimum(idx + w + 1, R)] - c[np.maximum(idx - w, 0)]
         with Bank(m1, m2, n=n, fs=fs, f_low=f_low, pn_x2=7, snr_threshold=6.0, window=W) as bank:
             for i, mt in enumerate(meta):
                 reg_max = region_response(bank, dte[i], mt["j0"])
@@ -223,10 +232,15 @@ def main():
                 k_rand.append(int(np.argmax(hit[rng.permutation(R)])) + 1)
                 for e, z in enumerate(single):
                     k_single[e].append(int(np.argmax(hit[np.argsort(-z[i], kind="stable")])) + 1)
+                for w_ in widths:
+                    k_smooth[w_].append(int(np.argmax(hit[np.argsort(-smooth(sc[i], w_), kind="stable")])) + 1)
             rep["detectable"] = detectable
             k_star = int(max(k_net)) if k_net else R
             rep["K_star"] = k_star
             rep["K_star_per_network"] = {str(args.seed + e): (int(max(k)) if k else R) for e, k in enumerate(k_single)}
+            rep["K_star_smoothed"] = {str(w_): (int(max(k)) if k else R) for w_, k in k_smooth.items()}
+            rep["K_99pct_smoothed"] = {str(w_): (int(np.ceil(np.percentile(k, 99))) if k else R)
+                                       for w_, k in k_smooth.items()}
             rep["K_star_random_order"] = int(max(k_rand)) if k_rand else R
             rep["K_median"] = float(np.median(k_net)) if k_net else None
             rep["K_median_random_order"] = float(np.median(k_rand)) if k_rand else None
