@@ -514,8 +514,8 @@ extern "C" cui_status cui_prescreen_create(const cui_prescreen_desc *d, cui_pres
     if (d->n / d->frame < 8 || d->n / d->frame > 256) return ps_fail(CUI_ERR_ARG, "n / frame must be in [8, 256]");
     if (d->regions < 2 || d->regions > 256) return ps_fail(CUI_ERR_ARG, "regions must be in [2, 256]");
     if (d->max_batch < 1 || d->max_batch > 4096) return ps_fail(CUI_ERR_ARG, "max_batch must be in [1, 4096]");
-    if (!(d->sample_rate > 0) || !(d->f_low > 0) || d->f_low >= d->sample_rate / 2)
-        return ps_fail(CUI_ERR_ARG, "need 0 < f_low < sample_rate / 2");
+    if (!(d->sample_rate > 0) || !std::isfinite(d->sample_rate) || !(d->f_low > 0) || d->f_low >= d->sample_rate / 2)
+        return ps_fail(CUI_ERR_ARG, "need a finite sample_rate and 0 < f_low < sample_rate / 2");
     cui_prescreen p = new cui_prescreen_s();
     p->desc = *d;
     p->stream = (cudaStream_t)d->stream;

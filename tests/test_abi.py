@@ -44,3 +44,17 @@ def test_argument_errors_need_no_gpu(lib):
     assert h.value is None
     st = lib.cui_filter_bank(None, None, 0, None)
     assert st == _lib.CUI_ERR_ARG
+
+
+def test_prescreen_create_rejects_bad_rates_without_a_gpu(lib):
+    # the band edges are cast to integers only after the rate and f_low are checked
+    from paper_1006_4644_gb300 import _lib
+
+    _lib.load_prescreen(lib)
+    h = ctypes.c_void_p()
+    for fs, f_low in ((float("inf"), 30.0), (float("nan"), 30.0), (4096.0, 2048.0), (4096.0, 1e300), (4096.0, 0.0)):
+        d = _lib.cui_prescreen_desc(n=1 << 16, sample_rate=fs, f_low=f_low, bands=16, frame=512, regions=100,
+                                    max_batch=64, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=1)
+        st = lib.cui_prescreen_create(ctypes.byref(d), ctypes.byref(h))
+        assert st == _lib.CUI_ERR_ARG and b"f_low" in lib.cui_last_error(), (fs, f_low)
+        assert h.value is None
