@@ -325,8 +325,9 @@ typedef struct {
     int32_t n1;    /* 64, 128 or 256 (subject to the kernels built for N) */
     int32_t ccols; /* 16, 32 or 64 */
     int32_t rpc;   /* rows per pass-2 CTA; 0: the streamed persistent pass 2
-                      (one CTA per SM, row pairs copied into shared memory by
-                      the bulk-copy engine), for n2 = N / n1 = 4096 */
+                      (one CTA per SM, rows copied into shared memory by the
+                      bulk-copy engine), for n2 = N / n1 = 4096 (row pairs)
+                      and 16384 (rows split four ways in frequency) */
     int32_t batch; /* templates per launch pair, >= 1 */
 } cui_tuning;
 
@@ -351,8 +352,8 @@ cui_status cui_bank_autotune(cui_bank bank, int32_t reps, cui_tuning *best, doub
 /* Bounds of the handle's device waits, for tests of the error path.  The
  * only spins in the library are the compare-and-swap loops that raise the
  * peak, window and cluster slots (at most cas_rounds rounds, default 2^20)
- * and, in the streamed pass 2 (tiling rpc 0), each team's wait for its row
- * pair to land in shared memory (at most copy_wait_ns ns on the GPU's global
+ * and, in the streamed pass 2 (tiling rpc 0), each wait for a row (pair) to
+ * land in shared memory (at most copy_wait_ns ns on the GPU's global
  * timer, default 10^9; 0 makes every such wait give up at once).  A wait
  * that runs out sets the device error word and
  * its kernel skips the rest of its work (the streamed pass 2 still waits up to

@@ -493,20 +493,22 @@ __device__ __forceinline__ int64_t p2_find(const E *v, int lt, float M, const in
 
 // Epilogue of a row (pair) whose last stage left output d = lg + i L/PPT +
 // r L/RL in v[i RL + r].  Output d of lane l is sample s = c_l + n1 d with
-// c_l = c + l n1/2; |z|^2 is compared before the (positive) scaling.  The
+// c_l = c + l n1/2; SPLIT (a row split four ways in frequency) puts 4 n1 in
+// place of n1, so s = c + 2 l n1 + 4 n1 d.  |z|^2 is compared before the
+// (positive) scaling.  The
 // maximum of |z|^2 over the NW warps that share `s_max` is reduced first
 // (`bar` is their barrier); only the threads that hold it then look for their
 // lowest sample with it and raise a peak slot: the template's global slot, or
 // with a shared `local` slot that one (so that no thread waits on an L2 round
 // trip here; the caller stores it to global memory later).
-template <int L, int RL, int PPT, int NW, typename E, typename Bar>
+template <int L, int RL, int PPT, int NW, bool SPLIT = false, typename E, typename Bar>
 __device__ __forceinline__ void p2_epilogue(const E *v, int lg, int c, int y, int t, const FusedArgs &p, float *s_max,
                                             Bar bar, Slot *local = nullptr)
 {
     constexpr int NL = lanes_of<E>;
     constexpr int TPR = L / PPT;
     const float inv = p.invnorm[t];
-    const int n1 = p.n1;
+    const int n1 = SPLIT ? 4 * p.n1 : p.n1; // sample step between consecutive outputs d
     const int64_t lo = p.lo, hi = p.hi;
     int64_t cl[NL];
     int dlo[NL], dhi[NL];
@@ -873,23 +875,27 @@ template <typename ST> __global__ void __launch_bounds__(2 * kStreamTeam, 1) k_p
             if (issued[q] > consumed[q] && !mbar_wait(&full[q], consumed[q] & 1, kCopyWaitNs)) atomicOr(p.err, 4);
 }
 
-// Streamed pass 2 for unpaired rows of 16384 points (N = 2^22 with n1 = 256).
-// A row (128 KiB in complex64) and its padded exchange buffer leave no room
-// for a second row, so the next row arrives in two halves: the first half into
-// a staging buffer S as soon as the current row's stage-0 inputs have been
-// read (it lands during stages 1-3), the second half into the first bytes of
-// the exchange buffer once the last stage has read it (it lands during the
-// last transform and the epilogue).  One persistent CTA of 1024 threads per
-// SM; the row's transform is that of k_pass2 (radices 4, 16, 16, 16, the last
-// two on half-warp groups), so the results are bit-identical.  Waits and the
-// error path as in k_pass2_stream.
+// Streamed pass 2 for rows of 16384 points (N = 2^22 with n1 = 256), on the
+// paired arithmetic of the 4096-point rows.  Split in frequency four ways,
+// b = b' + 4096 m and d = 4 k + q (b', k < 4096; m, q < 4):
+//   z[4 k + q] = sum_b' exp(2 pi i b' k / 4096) u_q[b'],
+//   u_q[b'] = exp(2 pi i q b' / 16384) sum_m i^(m q) x[b' + 4096 m],
+// a row is four independent 4096-point transforms.  Team 0 runs q = 0 and 2,
+// team 1 q = 1 and 3, each pair as the two lanes of one packed transform, the
+// transform of k_pass2_stream.  Each team computes its u from the row in
+// shared memory: the first half (b < 8192) in the staging buffer S, the second
+// half in the first bytes of team 0's exchange buffer.  One persistent CTA of
+// two teams per SM, one row at a time: once both teams have read the row, the
+// next row's first half is copied into S (it lands while the row is
+// transformed) and, once team 0's last stage has read its exchange buffer, the
+// next row's second half into that buffer (it lands during team 0's epilogue
+// and the rest of team 1's transform).  Waits and the error path as in
+// k_pass2_stream.
 constexpr int kStream16L = 16384;
-constexpr int kStream16Threads = 1024;
-
 template <typename ST> constexpr size_t s16_half_bytes() { return (size_t)(kStream16L / 2) * sizeof(ST); }
 template <typename ST> constexpr size_t s16_smem()
 {
-    return s16_half_bytes<ST>() + (size_t)padded<kStream16L>() * sizeof(float2);
+    return s16_half_bytes<ST>() + 2 * (size_t)padded<kStreamL>() * sizeof(c2);
 }
 
 template <typename ST> __device__ __forceinline__ float2 elem_from(ST q);
@@ -908,48 +914,53 @@ __device__ __forceinline__ void s16_issue_half(const FusedArgs &p, int item, int
     for (int q = 0; q < 2; ++q) bulk_load((char *)dst + q * (HALF / 2), src + q * (HALF / 2), HALF / 2, bar);
 }
 
-// Grid min(SMs, rows of the batch), 1024 threads; row i of the batch is
-// template y = i / n1, row c = i mod n1.
-template <typename ST> __global__ void __launch_bounds__(kStream16Threads, 1) k_pass2_stream16k(const FusedArgs p, int count)
+__device__ __forceinline__ Slot larger_slot(Slot a, Slot b) { return b.key > a.key ? b : a; }
+
+// Grid min(SMs, rows of the batch), 2 teams of 256 threads; row i of the batch
+// is template y = i / n1, row c = i mod n1.
+template <typename ST> __global__ void __launch_bounds__(2 * kStreamTeam, 1) k_pass2_split16k(const FusedArgs p, int count)
 {
-    constexpr int L = kStream16L, PPT = 16, TPR = kStream16Threads, NW = TPR / 32;
-    constexpr int R0 = 4, R1 = 16, R2 = 16, RL = 16, NSL = L / RL;
-    constexpr int T0 = PPT / R0;
+    constexpr int L = kStreamL, PPT = 16, R = 16, TPR = kStreamTeam, NW = TPR / 32;
+    constexpr int LP = padded<L>();
     constexpr unsigned HALF = (unsigned)s16_half_bytes<ST>();
     extern __shared__ __align__(128) float4 sm4[];
     const ST *S = reinterpret_cast<const ST *>(sm4);
-    float2 *row = reinterpret_cast<float2 *>((char *)sm4 + HALF);
-    const ST *Wraw = reinterpret_cast<const ST *>(row); // the second half of the next row, before stage 0 pads it
-    __shared__ float2 tw1[R0 * R1];
-    __shared__ float2 tw2[R0 * R1 * R2];
-    __shared__ float s_max[NW];
+    c2 *xb = reinterpret_cast<c2 *>((char *)sm4 + HALF);  // the teams' exchange buffers
+    const ST *W = reinterpret_cast<const ST *>(xb);       // the row's second half, in team 0's buffer
+    __shared__ float2 tw1[R * R];
+    __shared__ float s_max[2][NW];
     __shared__ __align__(8) uint64_t full;
     __shared__ int abort_flag, issued;
-    __shared__ Slot s_peak;
+    __shared__ Slot s_peak[2][2]; // [row parity][team]: each team's peak of the row
+    // exp(2 pi i q b' / 16384) at b' = lt + 256 r is rt[q][lt] st[q]^r (q = 1, 2, 3)
+    __shared__ float2 rt[3][kStreamTeam], st[3];
     const int tid = threadIdx.x;
-    const int lt = tid;
+    const int team = tid / TPR, lt = tid % TPR;
     const int lg = (lt & 15) * (L / 256) + (lt >> 4); // the last two stages on half-warp groups
+    c2 *row = xb + team * LP;
     const int n1 = p.n1;
     const int total = count * n1; // <= 64 templates x 256 rows in practice (4 GiB of Y at most)
     const int G = gridDim.x;
+    const int bar_team = 1 + team;
 
-    for (int m = tid; m < R0 * R1; m += TPR) tw1[m] = turn((m % R0) * (m / R0), R0 * R1);
-    for (int m = tid; m < R0 * R1 * R2; m += TPR) tw2[m] = turn((m % (R0 * R1)) * (m / (R0 * R1)), R0 * R1 * R2);
+    for (int m = tid; m < R * R; m += 2 * TPR) tw1[m] = turn((m % R) * (m / R), R * R);
+    for (int m = tid; m < 3 * TPR; m += 2 * TPR) rt[m / TPR][m % TPR] = turn((unsigned)((m / TPR + 1) * (m % TPR)), 4 * L);
+    if (tid < 3) st[tid] = turn((unsigned)(tid + 1), 64u);
     if (tid == 0) {
         mbar_init(&full, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
         issued = 0;
-        s_peak = Slot{0ull, 0u, 0u};
+        s_peak[0][0] = s_peak[0][1] = s_peak[1][0] = s_peak[1][1] = Slot{0ull, 0u, 0u};
     }
     __syncthreads();
     if (tid == 0 && (int)blockIdx.x < total) {
         issued = 1;
         mbar_expect_tx(&full, 2 * HALF);
         s16_issue_half<ST>(p, blockIdx.x, 0, (void *)S, &full);
-        s16_issue_half<ST>(p, blockIdx.x, 1, (void *)row, &full);
+        s16_issue_half<ST>(p, blockIdx.x, 1, (void *)W, &full);
     }
-    const float2 wl = p2_root<RL>(lg, NSL);
+    const float2 wl = p2_root<R>(lg, L / R);
 
     int j = 0, prev = -1;
     for (int i = blockIdx.x; i < total; i += G, ++j) {
@@ -957,23 +968,50 @@ template <typename ST> __global__ void __launch_bounds__(kStream16Threads, 1) k_
             abort_flag = 1;
             atomicOr(p.err, 4);
         }
-        float2 v[PPT];
+        c2 v[PPT];
+        // the twiddled lanes: team 0 q = 2, team 1 q = 1 and 3
+        const int qa = team ? 0 : 1;
+        const float2 st_a = st[qa];
+        float2 wa = rt[qa][lt];
+        if (team == 0) {
 #pragma unroll
-        for (int t = 0; t < T0; ++t)
-#pragma unroll
-            for (int r = 0; r < R0; ++r) {
-                const int x = lt + t * TPR + r * (L / R0); // quarter r of the row
-                v[t * R0 + r] = elem_from<ST>(r < 2 ? S[x] : Wraw[x - L / 2]);
+            for (int r = 0; r < R; ++r) {
+                const int b = lt + r * (L / R);
+                const float2 x0 = elem_from<ST>(S[b]), x1 = elem_from<ST>(S[b + L]);
+                const float2 x2 = elem_from<ST>(W[b]), x3 = elem_from<ST>(W[b + L]);
+                const float2 s0 = make_float2(x0.x + x2.x, x0.y + x2.y), s1 = make_float2(x1.x + x3.x, x1.y + x3.y);
+                const float2 u2 = cmul(make_float2(s0.x - s1.x, s0.y - s1.y), wa);
+                v[r] = c2{make_float2(s0.x + s1.x, u2.x), make_float2(s0.y + s1.y, u2.y)};
+                wa = cmul(wa, st_a);
             }
+        } else {
+            // both lanes twiddled: the twiddle pair (q = 1, 3) is a c2, stepped and
+            // applied with packed products
+            const float2 ta = rt[0][lt], tb = rt[2][lt], sa = st[0], sb = st[2];
+            c2 T = {make_float2(ta.x, tb.x), make_float2(ta.y, tb.y)};
+            const float2 sre = make_float2(sa.x, sb.x), sim = make_float2(sa.y, sb.y);
+            const float2 nsim = make_float2(-sa.y, -sb.y);
 #pragma unroll
-        for (int t = 0; t < T0; ++t) dft<R0, +1>(v + t * R0);
-        __syncthreads(); // every thread has read S and the raw half; abort_flag settled
+            for (int r = 0; r < R; ++r) {
+                const int b = lt + r * (L / R);
+                const float2 x0 = elem_from<ST>(S[b]), x1 = elem_from<ST>(S[b + L]);
+                const float2 x2 = elem_from<ST>(W[b]), x3 = elem_from<ST>(W[b + L]);
+                const float2 d0 = make_float2(x0.x - x2.x, x0.y - x2.y), d1 = make_float2(x1.x - x3.x, x1.y - x3.y);
+                // q = 1: d0 + i d1; q = 3: d0 - i d1 (and the negated imaginary parts)
+                const float2 pre = make_float2(d0.x - d1.y, d0.x + d1.y), pim = make_float2(d0.y + d1.x, d0.y - d1.x);
+                const float2 npim = make_float2(-d0.y - d1.x, d1.x - d0.y);
+                v[r] = c2{__ffma2_rn(T.im, npim, __fmul2_rn(T.re, pre)), __ffma2_rn(T.im, pre, __fmul2_rn(T.re, pim))};
+                T = c2{__ffma2_rn(T.im, nsim, __fmul2_rn(T.re, sre)), __ffma2_rn(T.im, sre, __fmul2_rn(T.re, sim))};
+            }
+        }
+        __syncthreads(); // both teams have read the row; abort_flag settled
         if (abort_flag) break;
         const bool has_next = i + G < total;
         if (tid == 0) {
-            if (prev >= 0) { // the previous row's peak (its CAS came before this barrier)
-                p.prec[prev] = s_peak;
-                s_peak = Slot{0ull, 0u, 0u};
+            if (prev >= 0) { // the previous row's peak (both teams raised their slots before this barrier)
+                Slot *q = s_peak[(j + 1) & 1];
+                p.prec[prev] = larger_slot(q[0], q[1]);
+                q[0] = q[1] = Slot{0ull, 0u, 0u};
             }
             if (has_next) { // the next row's first half lands while this row is transformed
                 issued += 1;
@@ -982,37 +1020,35 @@ template <typename ST> __global__ void __launch_bounds__(kStream16Threads, 1) k_
             }
         }
         prev = i;
-        p2_store<L, R0, 1, PPT>(v, row, lt);
-        __syncthreads();
         {
+            // Y is read exactly once: drop its L2 lines so that they are never written back
             const char *yb = (const char *)p.ywork + (size_t)i * 2 * HALF;
-            for (int m = tid; m < (int)(2 * HALF / 128); m += TPR)
+            for (int m = tid; m < (int)(2 * HALF / 128); m += 2 * TPR)
                 asm volatile("discard.global.L2 [%0], 128;" ::"l"(yb + (size_t)m * 128) : "memory");
         }
-        p2_stage<L, R1, R0, true, PPT>(v, row, lt, tw1);
-        __syncthreads();
-        p2_store<L, R1, R0, PPT>(v, row, lt);
-        __syncthreads();
-        p2_stage<L, R2, R0 * R1, true, PPT>(v, row, lg, tw2);
+        dft<R, +1>(v);
+        p2_store<L, R, 1, PPT>(v, row, lt);
+        named_sync(bar_team, TPR);
+        p2_stage<L, R, R, true, PPT>(v, row, lg, tw1);
         __syncwarp();
-        p2_store<L, R2, R0 * R1, PPT>(v, row, lg);
+        p2_store<L, R, R, PPT>(v, row, lg);
         __syncwarp();
-        p2_stage<L, RL, NSL, false, PPT>(v, row, lg, tw1, &wl);
+        p2_stage<L, R, L / R, false, PPT>(v, row, lg, tw1, &wl);
         const int y = i / n1, c = i % n1;
         const int t = p.order[p.base + y];
-        // the epilogue's barrier comes after every thread's last read of the
-        // exchange buffer: then the next row's second half may land in it
-        p2_epilogue<L, RL, PPT, NW>(
-            v, lg, c, y, t, p, s_max,
+        // the epilogue's team barrier follows every thread's last read of the
+        // team's exchange buffer: then team 0's may take the next row's second half
+        p2_epilogue<L, R, PPT, NW, true>(
+            v, lg, c + team * n1, y, t, p, s_max[team],
             [&] {
-                __syncthreads();
-                if (tid == 0 && has_next) s16_issue_half<ST>(p, i + G, 1, (void *)row, &full);
+                named_sync(bar_team, TPR);
+                if (tid == 0 && has_next) s16_issue_half<ST>(p, i + G, 1, (void *)W, &full);
             },
-            &s_peak);
+            &s_peak[j & 1][team]);
     }
     __syncthreads();
     if (tid == 0) {
-        if (prev >= 0) p.prec[prev] = s_peak; // the last row's peak
+        if (prev >= 0) p.prec[prev] = larger_slot(s_peak[(j + 1) & 1][0], s_peak[(j + 1) & 1][1]); // the last row's peak
         // a wait that gave up leaves that row's copies in flight: let them land first
         if (issued > j && !mbar_wait(&full, j & 1, kCopyWaitNs)) atomicOr(p.err, 4);
     }
@@ -1138,7 +1174,7 @@ template <typename ST> static cudaError_t run_pass2_stream(const FusedArgs &a, i
 
 template <typename ST> static cudaError_t run_pass2_stream16k(const FusedArgs &a, int count, cudaStream_t s)
 {
-    auto k = k_pass2_stream16k<ST>;
+    auto k = k_pass2_split16k<ST>;
     const size_t smem = s16_smem<ST>();
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
@@ -1146,7 +1182,7 @@ template <typename ST> static cudaError_t run_pass2_stream16k(const FusedArgs &a
     const int sms = sm_count();
     if (sms <= 0) return cudaErrorInvalidDevice;
     if (total <= 0) return cudaSuccess;
-    k<<<(unsigned)std::min<int64_t>(sms, total), kStream16Threads, smem, s>>>(a, count);
+    k<<<(unsigned)std::min<int64_t>(sms, total), 2 * kStreamTeam, smem, s>>>(a, count);
     return cudaGetLastError();
 }
 

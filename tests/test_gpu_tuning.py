@@ -106,14 +106,16 @@ def test_autotune_selects_a_valid_tiling():
                                                   (22, 256, 3, 2)])
 def test_streamed_pass2_equals_row_pair_kernel(log2n, n1, count, batch):
     """The streamed persistent pass 2 (rpc 0: rows copied into shared memory
-    by the bulk-copy engine; row pairs of 4096 points on two teams per CTA, or
-    unpaired 16384-point rows arriving in two halves) runs the same arithmetic
-    in the same order as the one-row-per-CTA kernels, so peaks and triggers are
-    bit-identical.  The cases cover fewer row pairs than SMs (one template at
-    2^20: 128 row pairs, the second team idle), both teams, CTAs with one and
-    with two rows at 2^22, ragged last batches, and a valid range that cuts
-    rows; the error word must stay clear (a bounded bulk-copy wait that gave up
-    would read CUI_ERR_TIMEOUT)."""
+    by the bulk-copy engine) against the one-row-per-CTA kernels.  Row pairs
+    of 4096 points on two teams per CTA run the same arithmetic in the same
+    order, so peaks and triggers are bit-identical.  The 16384-point rows of
+    2^22 are split four ways in frequency and transformed as two packed
+    4096-point transforms, a different order of the same sums: peaks agree to
+    FP32 rounding and both kernels match the FP64 oracle.  The cases cover
+    fewer row pairs than SMs (one template at 2^20: 128 row pairs, the second
+    team idle), both teams, CTAs with one and with two rows at 2^22, ragged
+    last batches, and a valid range that cuts rows; the error word must stay
+    clear (a bounded bulk-copy wait that gave up would read CUI_ERR_TIMEOUT)."""
     from paper_1006_4644_gb300 import Bank
 
     n = 1 << log2n
@@ -131,7 +133,14 @@ def test_streamed_pass2_equals_row_pair_kernel(log2n, n1, count, batch):
             b.filter()
             b.filter()  # a second call over the same buffers
             out[rpc] = (b.peaks(), b.triggers()[0])
-    assert np.array_equal(out[0][0], out[1][0])
-    assert np.array_equal(out[0][1], out[1][1])
+    if log2n < 22:
+        assert np.array_equal(out[0][0], out[1][0])
+        assert np.array_equal(out[0][1], out[1][1])
+    else:
+        a, b = out[0][0], out[1][0]
+        assert np.max(np.abs(a["snr"] - b["snr"]) / b["snr"]) < 2e-6
+        assert np.max(np.abs(np.angle(np.exp(1j * (a["phase"] - b["phase"]))))) < 2e-5
+        rep1 = compare_bank(w, dt, psd, out[1][0], out[1][1], range(w.n_templates), lo, hi, 1000, 4.5)
+        assert rep1.ok(), rep1
     rep = compare_bank(w, dt, psd, out[0][0], out[0][1], range(w.n_templates), lo, hi, 1000, 4.5)
     assert rep.ok(), rep
