@@ -168,14 +168,16 @@ def test_device_upload_matches_host_upload(seg16s):
     assert np.array_equal(a[0]["sample"], p["sample"]) and np.array_equal(a[0]["snr"], p["snr"])
 
 
-@pytest.mark.parametrize("wname,count", [("seg16s_bank64_pn2", 64), ("seg256s_bank1024_pn35", 24)])
+@pytest.mark.parametrize("wname,count", [("seg16s_bank64_pn2", 64), ("seg256s_bank1024_pn35", 24),
+                                         ("seg1024s_bank10k_pn35", 6)])
 def test_bf16_storage_within_its_bound(wname, count):
     """CUI_STORE_BF16 keeps Y (the spectrum between the FFT passes) as bf16
     pairs: each value rounds to 2^-9 relative, so rho may move by a few 1e-3.
     Against the FP64 oracle: every peak rho within 5e-3 relative, and every
     peak sample exact unless the oracle's rho at the reported sample is within
     5e-3 of its maximum.  At 2^20 this runs the streamed pass 2 (both teams)
-    with bf16 row pairs in its staging buffer."""
+    with bf16 row pairs in its staging buffer; at 2^22 the split pass 2 with
+    the bf16 row halves in its staging buffer and team 0's exchange buffer."""
     from paper_1006_4644_gb300 import CUI_STORE_BF16
 
     w = synth.WORKLOADS[wname]
@@ -184,8 +186,8 @@ def test_bf16_storage_within_its_bound(wname, count):
     order = np.unique(np.concatenate([np.arange(count), tmpl])).astype(np.int32)
     with _bank(w, CUI_STORE_BF16) as b:
         b.upload(strain, psd)
-        if w.n == 1 << 20:
-            assert b.tuning()["rpc"] == 0  # the default tiling at 2^20 is the streamed pass 2
+        if w.n >= 1 << 20:
+            assert b.tuning()["rpc"] == 0  # the default tiling at 2^20 and 2^22 is the streamed pass 2
         b.filter(order)
         peaks = b.peaks()
     worst = 0.0
