@@ -597,9 +597,8 @@ extern "C" cui_status cui_segment_upload(cui_bank b, const double *strain, int64
         CUI_TRY(cudaEventRecord(b->ev_psd, s), "psd check");
     }
     b->d_X = X;
-    launch_weighted_data(X, b->d_psd, b->d_amp, b->n, b->k_low, b->desc.sample_rate, b->d_scales, b->d_wbar,
-                         b->d_dS, b->plain_fp64, s);
-    launch_prefix(b->d_psd, b->d_amp, b->n, b->k_low, b->d_prefix, b->d_scan, s);
+    launch_segment_weights(X, b->d_psd, b->d_amp, b->n, b->k_low, b->desc.sample_rate, b->d_scales, b->d_wbar,
+                           b->d_dS, b->plain_fp64, b->d_prefix, b->d_scan, s);
     launch_template_norm(b->d_prefix, b->d_khi, b->band_lo, b->nt, b->desc.sample_rate, b->n, b->d_scales,
                          b->d_sigma2, b->d_invnorm, s);
     CUI_TRY(cudaGetLastError(), "cui_segment_upload");

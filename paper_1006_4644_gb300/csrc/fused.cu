@@ -1172,7 +1172,7 @@ template <typename ST> static cudaError_t run_pass2_stream(const FusedArgs &a, i
     return cudaGetLastError();
 }
 
-template <typename ST> static cudaError_t run_pass2_stream16k(const FusedArgs &a, int count, cudaStream_t s)
+template <typename ST> static cudaError_t run_pass2_split16k(const FusedArgs &a, int count, cudaStream_t s)
 {
     auto k = k_pass2_split16k<ST>;
     const size_t smem = s16_smem<ST>();
@@ -1190,7 +1190,7 @@ template <typename ST> static cudaError_t pass2_dispatch(const FusedArgs &a, int
 {
     const int L = a.n2, R = a.rpc;
     if (L == kStreamL && R == 0) return run_pass2_stream<ST>(a, count, s);
-    if (L == kStream16L && R == 0) return run_pass2_stream16k<ST>(a, count, s);
+    if (L == kStream16L && R == 0) return run_pass2_split16k<ST>(a, count, s);
     if (L == 64 && R == 32) return run_pass2<64, 32, ST, 4, 16, 1, 1>(a, count, s);
     if (L == 128 && R == 16) return run_pass2<128, 16, ST, 8, 16, 1, 1>(a, count, s);
     if (L == 256 && R == 8) return run_pass2<256, 8, ST, 16, 16, 1, 1>(a, count, s);

@@ -62,8 +62,11 @@ void launch_psd_check(const double *psd, int64_t k_lo, int64_t k_hi, unsigned lo
 // at the rate fs n / m; X the segment's bins 0 .. n/2, a and b m elements each
 void launch_band_series(const double2 *X, int64_t n, int log2m, int64_t ka, int64_t kb, const Twiddles &tw,
                         dfc *a, dfc *b, double *out, cudaStream_t s);
-void launch_weighted_data(const double2 *X, const double *psd, const double *amp, int64_t n, int k_low,
-                          double fs, SegScales *scales, float2 *wbar, void *dS, bool dS_fp64, cudaStream_t s);
+// wbar, dS (plain path), the segment scales and the prefix sums P of the
+// upload in two passes over the spectrum (work: one double per 2048 bins)
+void launch_segment_weights(const double2 *X, const double *psd, const double *amp, int64_t n, int k_low, double fs,
+                            SegScales *scales, float2 *wbar, void *dS, bool dS_fp64, double *prefix, double *work,
+                            cudaStream_t s);
 void launch_prefix(const double *psd, const double *amp, int64_t n, int k_low, double *prefix, double *work,
                    cudaStream_t s);
 // sigma^2 and the fused normaliser of every template over [klo, khi[t])

@@ -293,31 +293,32 @@ void launch_psd_check(const double *psd, int64_t k_lo, int64_t k_hi, unsigned lo
 // Non-negative doubles compare as unsigned integers, so atomicMax on their
 // bits is a floating-point max.
 __device__ __forceinline__ int exp_field(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF); }
+constexpr int kNoExp = -(1 << 20);
 
-__global__ void k_wmax(const double2 *__restrict__ X, const double *__restrict__ psd, const double *__restrict__ amp,
-                       int64_t nh, int k_low, int e_fs, SegScales *sc)
+// raise the exponent maxima (ew: weighted data, ed: plain data) by bin k of the band
+__device__ __forceinline__ void exp_max_bin(const double2 *__restrict__ X, const double *__restrict__ psd,
+                                            const double *__restrict__ amp, int64_t k, int &ew, int &ed)
 {
-    constexpr int kNone = -(1 << 20);
+    const double2 x = X[k];
+    const long long bx = __double_as_longlong(x.x) & 0x7FFFFFFFFFFFFFFFll;
+    const long long by = __double_as_longlong(x.y) & 0x7FFFFFFFFFFFFFFFll;
+    const int ex = (int)((bx > by ? bx : by) >> 52); // 0 for zero (and subnormal) bins
+    if (ex == 0) return;
+    const int d = ex - exp_field(psd[k]);
+    ed = max(ed, d);
+    ew = max(ew, d + exp_field(amp[k]) - 1023);
+}
+
+// the block's exponent maxima, then one atomic pair per block on the two
+// shared addresses
+__device__ __forceinline__ void block_exp_max(int ew, int ed, int e_fs, SegScales *sc)
+{
     __shared__ int s_ew[32], s_ed[32];
-    int ew = kNone, ed = kNone;
-    for (int64_t k = k_low + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nh;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const double2 x = X[k];
-        const long long bx = __double_as_longlong(x.x) & 0x7FFFFFFFFFFFFFFFll;
-        const long long by = __double_as_longlong(x.y) & 0x7FFFFFFFFFFFFFFFll;
-        const int ex = (int)((bx > by ? bx : by) >> 52); // 0 for zero (and subnormal) bins
-        if (ex == 0) continue;
-        const int d = ex - exp_field(psd[k]);
-        ed = max(ed, d);
-        ew = max(ew, d + exp_field(amp[k]) - 1023);
-    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, o));
         ed = max(ed, __shfl_xor_sync(0xffffffffu, ed, o));
     }
-    // then over the block's warps, so that one atomic pair per block (not per
-    // warp) reaches the two shared addresses
     const int wid = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
         s_ew[wid] = ew;
@@ -329,7 +330,7 @@ __global__ void k_wmax(const double2 *__restrict__ X, const double *__restrict__
             ew = max(ew, s_ew[w]);
             ed = max(ed, s_ed[w]);
         }
-        if (ed != kNone) {
+        if (ed != kNoExp) {
             const double mw = ldexp(1.0, ew + e_fs), md = ldexp(1.0, ed + e_fs);
             atomicMax((unsigned long long *)&sc->max_w, (unsigned long long)__double_as_longlong(mw));
             atomicMax((unsigned long long *)&sc->max_d, (unsigned long long)__double_as_longlong(md));
@@ -345,37 +346,21 @@ __device__ __forceinline__ double pow2_scale(double m)
 
 // wbar_k = scale_w d~_k amp_k / S_k and dS_k = scale_d d~_k / S_k on the band
 // [k_low, N/2), zero below it.
-__global__ void k_wwrite(const double2 *__restrict__ X, const double *__restrict__ psd,
-                         const double *__restrict__ amp, int64_t nh, int k_low, double inv_fs, SegScales *sc,
-                         float2 *__restrict__ wbar, void *dS, bool dS_fp64)
+__device__ __forceinline__ void weighted_bin(const double2 *__restrict__ X, const double *__restrict__ psd,
+                                             const double *__restrict__ amp, int64_t k, int k_low, double inv_fs,
+                                             double sw, double sd, float2 *__restrict__ wbar, void *dS,
+                                             bool dS_fp64)
 {
-    const double sw = pow2_scale(sc->max_w), sd = pow2_scale(sc->max_d);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        sc->scale_w = sw;
-        sc->scale_d = sd;
+    double2 w = make_double2(0.0, 0.0);
+    if (k >= k_low) {
+        double f = inv_fs / psd[k];
+        w = make_double2(X[k].x * f, X[k].y * f);
     }
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nh; k += (int64_t)gridDim.x * blockDim.x) {
-        double2 w = make_double2(0.0, 0.0);
-        if (k >= k_low) {
-            double f = inv_fs / psd[k];
-            w = make_double2(X[k].x * f, X[k].y * f);
-        }
-        wbar[k] = make_float2((float)(w.x * amp[k] * sw), (float)(w.y * amp[k] * sw));
-        if (dS) {
-            if (dS_fp64) ((double2 *)dS)[k] = make_double2(w.x * sd, w.y * sd);
-            else ((float2 *)dS)[k] = make_float2((float)(w.x * sd), (float)(w.y * sd));
-        }
+    wbar[k] = make_float2((float)(w.x * amp[k] * sw), (float)(w.y * amp[k] * sw));
+    if (dS) {
+        if (dS_fp64) ((double2 *)dS)[k] = make_double2(w.x * sd, w.y * sd);
+        else ((float2 *)dS)[k] = make_float2((float)(w.x * sd), (float)(w.y * sd));
     }
-}
-
-void launch_weighted_data(const double2 *X, const double *psd, const double *amp, int64_t n, int k_low, double fs,
-                          SegScales *scales, float2 *wbar, void *dS, bool dS_fp64, cudaStream_t s)
-{
-    const int64_t nh = n / 2;
-    cudaMemsetAsync(scales, 0, sizeof(SegScales), s);
-    k_wmax<<<1216, 256, 0, s>>>(X, psd, amp, nh, k_low, ilogb(1.0 / fs), scales);
-    k_wwrite<<<1216, 256, 0, s>>>(X, psd, amp, nh, k_low, 1.0 / fs, scales, wbar, dS, dS_fp64);
-    launched(2);
 }
 
 // ------------------------------------------------------------ prefix sums ---
@@ -476,6 +461,83 @@ void launch_prefix(const double *psd, const double *amp, int64_t n, int k_low, d
     k_scan_sums<<<nb, kScanThreads, 0, s>>>(psd, amp, nh, k_low, work);
     k_scan_offsets<<<1, 1024, 0, s>>>(work, nb);
     k_scan_write<<<nb, kScanThreads, 0, s>>>(psd, amp, nh, k_low, work, prefix);
+    launched(3);
+}
+
+// The weighted data and the prefix sums in two passes over the spectrum, for
+// the bank's upload.  Pass 1 (one block per kScanBlock bins, kScanPer
+// consecutive bins per thread, as k_scan_sums) takes the block sums of P's
+// terms and the exponent maxima; k_scan_offsets scans the block sums; pass 2
+// (the same blocks) writes wbar and dS (coalesced: bin base + t + r blockDim)
+// and the prefix sums (the per-thread grouping of pass 1, so the offsets
+// match the sums bit for bit).
+__global__ void __launch_bounds__(kScanThreads) k_seg_reduce(const double2 *__restrict__ X,
+                                                             const double *__restrict__ psd,
+                                                             const double *__restrict__ amp, int64_t nh, int k_low,
+                                                             int e_fs, SegScales *sc, double *bsum)
+{
+    __shared__ double sh[32];
+    const int64_t k0 = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
+    double s = 0.0;
+    int ew = kNoExp, ed = kNoExp;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        const int64_t k = k0 + i;
+        s += g_term(psd, amp, k, nh, k_low);
+        if (k >= k_low && k < nh) exp_max_bin(X, psd, amp, k, ew, ed);
+    }
+    double tot;
+    block_exclusive_scan(s, sh, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+    block_exp_max(ew, ed, e_fs, sc);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_seg_write(const double2 *__restrict__ X,
+                                                            const double *__restrict__ psd,
+                                                            const double *__restrict__ amp, int64_t nh, int k_low,
+                                                            double inv_fs, SegScales *sc, float2 *__restrict__ wbar,
+                                                            void *dS, bool dS_fp64, const double *boff,
+                                                            double *prefix)
+{
+    __shared__ double sh[32];
+    const double sw = pow2_scale(sc->max_w), sd = pow2_scale(sc->max_d);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->scale_w = sw;
+        sc->scale_d = sd;
+    }
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        const int64_t k = base + threadIdx.x + i * kScanThreads;
+        if (k < nh) weighted_bin(X, psd, amp, k, k_low, inv_fs, sw, sd, wbar, dS, dS_fp64);
+    }
+    const int64_t k0 = base + threadIdx.x * kScanPer;
+    double g[kScanPer];
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        g[i] = g_term(psd, amp, k0 + i, nh, k_low);
+        s += g[i];
+    }
+    double tot;
+    double run = boff[blockIdx.x] + block_exclusive_scan(s, sh, &tot);
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        if (k0 + i <= nh) prefix[k0 + i] = run;
+        run += g[i];
+    }
+}
+
+void launch_segment_weights(const double2 *X, const double *psd, const double *amp, int64_t n, int k_low, double fs,
+                            SegScales *scales, float2 *wbar, void *dS, bool dS_fp64, double *prefix, double *work,
+                            cudaStream_t s)
+{
+    const int64_t nh = n / 2;
+    const int nb = (int)((nh + 1 + kScanBlock - 1) / kScanBlock); // nh + 1 prefix values
+    cudaMemsetAsync(scales, 0, sizeof(SegScales), s);
+    k_seg_reduce<<<nb, kScanThreads, 0, s>>>(X, psd, amp, nh, k_low, ilogb(1.0 / fs), scales, work);
+    k_scan_offsets<<<1, 1024, 0, s>>>(work, nb);
+    k_seg_write<<<nb, kScanThreads, 0, s>>>(X, psd, amp, nh, k_low, 1.0 / fs, scales, wbar, dS, dS_fp64, work, prefix);
     launched(3);
 }
 
