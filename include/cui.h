@@ -218,8 +218,11 @@ cui_status cui_bank_set_band(cui_bank bank, double f_lo, double f_hi);
  * segment's first sample, taken modulo T = N / fs):
  *   z_i = 4 df sum_{k in B_i} d~_k conj(h~_k) / S_k exp(+2 pi i k df t_i),
  *   sigma_i^2 = 4 df sum_{k in B_i} |h~_k|^2 / S_k,
- * h~_k = f_k^(-7/6) exp(-i Psi(f_k)) generated exactly as the filter generates
- * it, B_i = [max(f_lo, f_low), f_hi) cut to the template's own band [f_low,
+ * h~_k = f_k^(-7/6) exp(-i Psi(f_k)) generated by the filter's method
+ * (double-float phase anchors, one per block of 32 bins, or of the tiling's
+ * ccols where N / n1 < 32, FP32 per bin; the
+ * phase within 1e-6 cycles of the FP64 value), B_i = [max(f_lo, f_low), f_hi)
+ * cut to the template's own band [f_low,
  * f_isco) (f_hi <= 0: no upper limit), whatever cui_bank_set_band holds.  At a
  * sample time j / fs over the filter's band, z_i / sigma is the filter's rho
  * with its phase.  Both are in physical units (strain and PSD as uploaded,

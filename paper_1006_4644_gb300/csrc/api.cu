@@ -193,6 +193,13 @@ struct cui_bank_s {
     int32_t *d_kex = nullptr;
     float2 *d_gexact = nullptr;
     std::vector<int32_t> h_kex;
+    // anchors and exact-phase bounds of the chi^2 and band-sum kernels: blocks
+    // of pf_ccols bins (the filter's own tables when its ccols is that width)
+    double *d_basis_pf = nullptr;
+    float2 *d_basis_df_pf = nullptr;
+    int32_t *d_kex_pf = nullptr;
+    int pf_ccols = 0;
+    std::vector<int32_t> h_kex_pf;
     std::vector<double> h_c0;   // leading phase coefficient of every template
     std::vector<double> h_mass; // (M in seconds, eta) of every template
     int kx = 0;
@@ -316,6 +323,9 @@ static void release(cui_bank b)
                     b->d_order, b->d_psd_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (b->d_basis_pf != b->d_basis) cudaFree(b->d_basis_pf);
+    if (b->d_basis_df_pf != b->d_basis_df) cudaFree(b->d_basis_df_pf);
+    if (b->d_kex_pf != b->d_kex) cudaFree(b->d_kex_pf);
     for (auto &m : b->marks) {
         cudaEventDestroy(m.a);
         cudaEventDestroy(m.b);
@@ -334,8 +344,24 @@ static void release(cui_bank b)
 
 extern "C" const char *cui_last_error(void) { return g_err.c_str(); }
 
+constexpr int kPostCols = 32; // anchor block of the chi^2 and band-sum kernels
+
+// One anchor table (blocks of ccols bins below N/2) and its exact-phase bounds.
+static cudaError_t build_anchor_set(cui_bank b, int n1, int n2, int ccols, const std::vector<int32_t> &kex,
+                                    double **basis, float2 **basis_df, int32_t **d_kex)
+{
+    const int64_t na = (int64_t)(n1 / 2) * (n2 / ccols);
+    cudaError_t e;
+    if ((e = dalloc(basis, na * kNB)) != cudaSuccess) return e;
+    if ((e = dalloc(basis_df, na * kNB)) != cudaSuccess) return e;
+    if ((e = dalloc(d_kex, b->nt)) != cudaSuccess) return e;
+    launch_basis_table(*basis, *basis_df, n1, n2, ccols, b->stream);
+    return cudaMemcpyAsync(*d_kex, kex.data(), sizeof(int32_t) * b->nt, cudaMemcpyHostToDevice, b->stream);
+}
+
 // Anchor basis table, per-template exact-phase bounds and the per-bin exact
-// table for a tiling (n1 rows, ccols columns per pass-1 CTA).  Synchronous.
+// table for a tiling (n1 rows, ccols columns per pass-1 CTA), and the tables
+// of the chi^2 and band-sum kernels.  Synchronous.
 static cudaError_t build_phase_tables(cui_bank b, int n1, int ccols)
 {
     const cudaStream_t s = b->stream;
@@ -345,6 +371,12 @@ static cudaError_t build_phase_tables(cui_bank b, int n1, int ccols)
         cudaGraphExecDestroy(b->gexec);
         b->gexec = nullptr;
     }
+    if (b->d_basis_pf != b->d_basis) cudaFree(b->d_basis_pf);
+    if (b->d_basis_df_pf != b->d_basis_df) cudaFree(b->d_basis_df_pf);
+    if (b->d_kex_pf != b->d_kex) cudaFree(b->d_kex_pf);
+    b->d_basis_pf = nullptr;
+    b->d_basis_df_pf = nullptr;
+    b->d_kex_pf = nullptr;
     for (void *p : {(void *)b->d_basis, (void *)b->d_basis_df, (void *)b->d_kex, (void *)b->d_gexact})
         if (p) cudaFree(p);
     b->d_basis = nullptr;
@@ -352,22 +384,32 @@ static cudaError_t build_phase_tables(cui_bank b, int n1, int ccols)
     b->d_kex = nullptr;
     b->d_gexact = nullptr;
     const int n2 = (int)(b->n / n1);
-    const int64_t na = (int64_t)(n1 / 2) * (n2 / ccols);
+    // the chi^2 and band-sum kernels evaluate one anchor per block of bins, a
+    // larger share of their work than of pass 1's: they use blocks of
+    // kPostCols bins whatever the filter's tiling
+    const int pf = (ccols != kPostCols && n2 % kPostCols == 0) ? kPostCols : ccols;
+    b->pf_ccols = pf;
     b->h_kex.resize(b->nt);
+    b->h_kex_pf.resize(b->nt);
     b->kx = 0;
     for (int64_t t = 0; t < b->nt; ++t) {
         b->h_kex[t] = exact_bound(b->h_c0[t], ccols, b->nh);
-        b->kx = std::max(b->kx, b->h_kex[t]);
+        b->h_kex_pf[t] = exact_bound(b->h_c0[t], pf, b->nh);
+        b->kx = std::max(b->kx, std::max(b->h_kex[t], b->h_kex_pf[t])); // one exact table serves both
     }
-    if ((e = dalloc(&b->d_basis, na * kNB)) != cudaSuccess) return e;
-    if ((e = dalloc(&b->d_basis_df, na * kNB)) != cudaSuccess) return e;
-    if ((e = dalloc(&b->d_kex, b->nt)) != cudaSuccess) return e;
+    if ((e = build_anchor_set(b, n1, n2, ccols, b->h_kex, &b->d_basis, &b->d_basis_df, &b->d_kex)) != cudaSuccess)
+        return e;
+    if (pf == ccols) {
+        b->d_basis_pf = b->d_basis;
+        b->d_basis_df_pf = b->d_basis_df;
+        b->d_kex_pf = b->d_kex;
+    } else if ((e = build_anchor_set(b, n1, n2, pf, b->h_kex_pf, &b->d_basis_pf, &b->d_basis_df_pf, &b->d_kex_pf)) !=
+               cudaSuccess) {
+        return e;
+    }
     if ((e = dalloc(&b->d_gexact, (int64_t)std::max(1, b->kx) * kNB)) != cudaSuccess) return e;
-    launch_basis_table(b->d_basis, b->d_basis_df, n1, n2, ccols, s);
     launch_exact_table(b->d_gexact, b->kx, s);
     fused_set_consts(make_deriv_consts(), s);
-    e = cudaMemcpyAsync(b->d_kex, b->h_kex.data(), sizeof(int32_t) * b->nt, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(s);
 }
 
@@ -651,6 +693,18 @@ static FusedArgs fused_args(cui_bank b, const int32_t *order, int64_t base)
     a.thr2 = (float)(b->desc.snr_threshold * b->desc.snr_threshold);
     a.fp64 = (b->desc.flags & CUI_PSI_FP64) != 0;
     a.bf16 = (b->desc.flags & CUI_STORE_BF16) != 0;
+    return a;
+}
+
+// The arguments of the chi^2 and band-sum kernels: the filter's, with the
+// anchors of their own block width.
+static FusedArgs fused_args_post(cui_bank b)
+{
+    FusedArgs a = fused_args(b, b->d_iota, 0);
+    a.basis = b->d_basis_pf;
+    a.basis_df = b->d_basis_df_pf;
+    a.kex = b->d_kex_pf;
+    a.ccols = b->pf_ccols;
     return a;
 }
 
@@ -1131,7 +1185,7 @@ extern "C" cui_status cui_trigger_chisq(cui_bank b, int32_t bands, const cui_tri
     if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(float) * 2 * n);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_trig, h.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = launch_chisq(fused_args(b, b->d_iota, 0), b->d_prefix, d_trig, (int)n, bands, d_out, d_out + n, s);
+        e = launch_chisq(fused_args_post(b), b->d_prefix, d_trig, (int)n, bands, d_out, d_out + n, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_chisq, d_out, sizeof(float) * n, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && host_rho)
         e = cudaMemcpyAsync(host_rho, d_out + n, sizeof(float) * n, cudaMemcpyDeviceToHost, s);
@@ -1252,7 +1306,7 @@ static cudaError_t band_queue(cui_bank b, const BandQuery &q, BandBufs &bufs)
     if (e == cudaSuccess) e = cudaMemcpyAsync(bufs.t, q.t.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bufs.u, q.u.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = launch_band(fused_args(b, b->d_iota, 0), b->d_prefix, b->d_khi0, bufs.t, bufs.u, (int)n, q.ka, q.kb,
+        e = launch_band(fused_args_post(b), b->d_prefix, b->d_khi0, bufs.t, bufs.u, (int)n, q.ka, q.kb,
                         b->d_scales, q.zfac, q.sfac, bufs.out, s);
     return e;
 }

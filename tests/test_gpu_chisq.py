@@ -27,7 +27,7 @@ def _check(w, dt, psd, trig, chi, rho, bands):
         sel = np.nonzero(trig["tmpl"] == t)[0]
         c_o, r_o = oracle.chisq(dt, psd, m1[t], m2[t], w.pn_x2, w.f_low, w.fs, w.n, trig["sample"][sel], bands)
         assert np.allclose(rho[sel], r_o, rtol=1e-3), (t, rho[sel], r_o)
-        assert np.allclose(trig["snr"][sel], rho[sel], rtol=1e-4)  # same generation as the filter
+        assert np.allclose(trig["snr"][sel], rho[sel], rtol=1e-4)  # the filter's generation method
         tol = 1e-3 * (c_o + 2 * bands) + 1e-4 * r_o ** 2
         assert np.all(np.abs(chi[sel] - c_o) <= tol), (t, chi[sel], c_o)
 
