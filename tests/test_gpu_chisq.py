@@ -95,3 +95,33 @@ def test_chisq_errors():
         with pytest.raises(CuiError) as e:
             b.trigger_chisq(rec, 16)
         assert e.value.status == _lib.CUI_ERR_STATE
+
+
+def test_post_filter_sums_do_not_depend_on_the_filter_tiling():
+    """chi^2 and the band correlators use their own anchor tables (one anchor
+    per 32 bins), so for the same triggers and queries their results are the
+    same bit for bit whether the filter runs on 16 or 32 columns per pass-1
+    CTA."""
+    from paper_1006_4644_gb300 import Bank
+
+    w = synth.WORKLOADS["seg256s_bank1024_pn35"]
+    strain, psd, _, _ = make_segment(w)
+    m1, m2 = w.masses()
+    m1, m2 = m1[:64], m2[:64]
+    tm = np.arange(0, 64, 5, dtype=np.int32)
+    ts = 0.37 * tm + 1.5
+    pick, out = None, []
+    for ccols in (16, 32):
+        with Bank(m1, m2, n=w.n, fs=w.fs, f_low=w.f_low, pn_x2=w.pn_x2, snr_threshold=5.0) as b:
+            b.upload(strain, psd)
+            b.set_tuning(256, ccols, 0, 64)
+            if pick is None:
+                b.filter()
+                trig, _ = b.triggers()
+                pick = trig[:32]
+            chi, rho = b.trigger_chisq(pick, 16)
+            z, s2 = b.band_correlate(tm, ts, 0.0, 80.0)
+            out.append((chi, rho, z, s2))
+    assert len(pick) > 0
+    for a, b_ in zip(out[0], out[1]):
+        assert np.array_equal(a, b_)
